@@ -1,0 +1,267 @@
+"""Python face of the CPU oracle (test infrastructure).
+
+Only tests/, ``__graft_entry__.smoke()`` and bench.py's ``cpu_baseline`` leg may
+import this module. It loads ``liboracle.so`` (plain C, complex128, built from
+``qv_oracle.c`` by ``build_oracle()``) and shares no code with the CUDA path.
+
+Gradients here are computed by re-simulation only: the exact parameter-shift
+rule and central finite differences. Neither uses the adjoint method.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from typing import Iterable, List, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qv_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+_KIND = {"h": 0, "x": 1, "y": 2, "z": 3, "s": 4, "sdg": 5, "t": 6, "tdg": 7,
+         "rx": 8, "ry": 9, "rz": 10, "p": 11, "u3": 12, "matrix": 13, "swap": 14}
+
+
+class OrcGate(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("target", ctypes.c_int32),
+                ("target2", ctypes.c_int32), ("ctrl", ctypes.c_int32),
+                ("theta", ctypes.c_double * 3), ("m", ctypes.c_double * 8)]
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile qv_oracle.c into liboracle.so with gcc (plain -O2, no -ffast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def load(path: str):
+    """Load an oracle library at ``path`` and declare its signatures."""
+    L = ctypes.CDLL(path)
+    c128p = ctypes.c_void_p
+    L.orc_gate_matrix.argtypes = [ctypes.POINTER(OrcGate), c128p]
+    L.orc_gate_matrix.restype = ctypes.c_int
+    L.orc_apply_1q.argtypes = [c128p, ctypes.c_int, ctypes.c_int, c128p]
+    L.orc_apply_controlled.argtypes = [c128p, ctypes.c_int, ctypes.c_int, ctypes.c_int, c128p]
+    L.orc_apply_swap.argtypes = [c128p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.orc_run.argtypes = [c128p, ctypes.c_int, ctypes.POINTER(OrcGate), ctypes.c_int64]
+    L.orc_run.restype = ctypes.c_int64
+    L.orc_basis.argtypes = [c128p, ctypes.c_int, ctypes.c_uint64]
+    L.orc_permute.argtypes = [c128p, c128p, ctypes.c_int, ctypes.c_void_p]
+    L.orc_norm2.argtypes = [c128p, ctypes.c_int]
+    L.orc_norm2.restype = ctypes.c_double
+    L.orc_expect_z.argtypes = [c128p, ctypes.c_int, ctypes.c_void_p]
+    L.orc_expect_pauli.argtypes = [c128p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64]
+    L.orc_expect_pauli.restype = ctypes.c_double
+    L.orc_apply_pauli_sum.argtypes = [c128p, c128p, ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
+    L.orc_inner.argtypes = [c128p, c128p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                            ctypes.POINTER(ctypes.c_double)]
+    return L
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = load(build_oracle())
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def _check_state(psi: np.ndarray) -> int:
+    if psi.dtype != np.complex128 or not psi.flags.c_contiguous:
+        raise TypeError("oracle states are contiguous complex128 arrays")
+    n = int(psi.size).bit_length() - 1
+    if psi.size != (1 << n):
+        raise ValueError("state length must be a power of two")
+    return n
+
+
+def to_orc_gates(gates: Sequence) -> ctypes.Array:
+    arr = (OrcGate * max(1, len(gates)))()
+    for i, g in enumerate(gates):
+        o = arr[i]
+        o.kind = _KIND[g.kind]
+        o.target = g.target
+        o.target2 = g.target2
+        o.ctrl = g.ctrl
+        for e in range(3):
+            o.theta[e] = g.theta[e]
+        if g.matrix is not None:
+            for e, z in enumerate(g.matrix):
+                o.m[2 * e] = complex(z).real
+                o.m[2 * e + 1] = complex(z).imag
+    return arr
+
+
+# ----------------------------------------------------------------------------
+# state construction and gate application
+# ----------------------------------------------------------------------------
+def basis(n: int, j: int = 0) -> np.ndarray:
+    psi = np.empty(1 << n, dtype=np.complex128)
+    lib().orc_basis(_ptr(psi), n, j)
+    return psi
+
+
+def gate_matrix(g) -> np.ndarray:
+    U = np.zeros(4, dtype=np.complex128)
+    arr = to_orc_gates([g])
+    if lib().orc_gate_matrix(arr, _ptr(U)):
+        raise ValueError("no matrix for gate kind %r" % (g.kind,))
+    return U.reshape(2, 2)
+
+
+def apply_1q(psi: np.ndarray, target: int, U) -> np.ndarray:
+    """Eq. 5 in place on ``psi``; returns psi."""
+    n = _check_state(psi)
+    if not 0 <= target < n:
+        raise ValueError("target out of range")
+    Uc = np.ascontiguousarray(np.asarray(U, dtype=np.complex128).reshape(4))
+    lib().orc_apply_1q(_ptr(psi), n, target, _ptr(Uc))
+    return psi
+
+
+def apply_controlled(psi: np.ndarray, ctrl: int, target: int, U) -> np.ndarray:
+    n = _check_state(psi)
+    if not (0 <= target < n and 0 <= ctrl < n and ctrl != target):
+        raise ValueError("bad control/target")
+    Uc = np.ascontiguousarray(np.asarray(U, dtype=np.complex128).reshape(4))
+    lib().orc_apply_controlled(_ptr(psi), n, ctrl, target, _ptr(Uc))
+    return psi
+
+
+def apply_swap(psi: np.ndarray, a: int, b: int) -> np.ndarray:
+    n = _check_state(psi)
+    lib().orc_apply_swap(_ptr(psi), n, a, b)
+    return psi
+
+
+def run(n: int, gates: Sequence, psi: np.ndarray | None = None) -> np.ndarray:
+    """Apply ``gates`` in order to ``psi`` (default |0...0>), in place; returns psi."""
+    if psi is None:
+        psi = basis(n, 0)
+    if _check_state(psi) != n:
+        raise ValueError("state size does not match n")
+    if len(gates) == 0:
+        return psi
+    arr = to_orc_gates(gates)
+    bad = lib().orc_run(_ptr(psi), n, arr, len(gates))
+    if bad:
+        raise ValueError("bad gate at index %d: %r" % (bad - 1, gates[bad - 1]))
+    return psi
+
+
+def permute(psi: np.ndarray, perm: Sequence[int]) -> np.ndarray:
+    """out[pi(i)] = psi[i] where bit q of i moves to bit perm[q]."""
+    n = _check_state(psi)
+    p = np.ascontiguousarray(np.asarray(perm, dtype=np.int32))
+    if sorted(p.tolist()) != list(range(n)):
+        raise ValueError("not a permutation")
+    out = np.empty_like(psi)
+    lib().orc_permute(_ptr(psi), _ptr(out), n, _ptr(p))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# reductions
+# ----------------------------------------------------------------------------
+def norm2(psi: np.ndarray) -> float:
+    return lib().orc_norm2(_ptr(psi), _check_state(psi))
+
+
+def expect_z(psi: np.ndarray) -> np.ndarray:
+    n = _check_state(psi)
+    out = np.zeros(n)
+    lib().orc_expect_z(_ptr(psi), n, _ptr(out))
+    return out
+
+
+def expect_pauli(psi: np.ndarray, xmask: int, zmask: int) -> float:
+    return lib().orc_expect_pauli(_ptr(psi), _check_state(psi), xmask, zmask)
+
+
+def expect_terms(psi: np.ndarray, terms: Iterable[Tuple[float, int, int]]) -> float:
+    """<psi|H|psi> for H = sum coeff * P(xmask, zmask)."""
+    return float(sum(c * expect_pauli(psi, x, z) for c, x, z in terms))
+
+
+def apply_pauli_sum(psi: np.ndarray, terms: Sequence[Tuple[float, int, int]]) -> np.ndarray:
+    n = _check_state(psi)
+    c = np.array([t[0] for t in terms], dtype=np.float64)
+    x = np.array([t[1] for t in terms], dtype=np.uint64)
+    z = np.array([t[2] for t in terms], dtype=np.uint64)
+    out = np.empty_like(psi)
+    lib().orc_apply_pauli_sum(_ptr(psi), _ptr(out), n, _ptr(c), _ptr(x), _ptr(z), len(terms))
+    return out
+
+
+def inner(a: np.ndarray, b: np.ndarray) -> complex:
+    re, im = ctypes.c_double(), ctypes.c_double()
+    lib().orc_inner(_ptr(a), _ptr(b), _check_state(a), ctypes.byref(re), ctypes.byref(im))
+    return complex(re.value, im.value)
+
+
+# ----------------------------------------------------------------------------
+# gradients by re-simulation
+# ----------------------------------------------------------------------------
+def energy(n: int, gates: Sequence, terms, psi0: np.ndarray | None = None) -> float:
+    psi = run(n, gates, None if psi0 is None else psi0.copy())
+    return expect_terms(psi, terms)
+
+
+def _shifted(gates: Sequence, gi: int, slot: int, delta: float) -> List:
+    g = gates[gi]
+    th = list(g.theta)
+    th[slot] += delta
+    out = list(gates)
+    out[gi] = g._replace(theta=tuple(th))
+    return out
+
+
+def _occurrences(gates: Sequence, nparams: int):
+    occ = [[] for _ in range(nparams)]
+    for gi, g in enumerate(gates):
+        for slot, p in enumerate(g.param):
+            if p >= 0:
+                occ[p].append((gi, slot))
+    return occ
+
+
+def param_shift_grad(n: int, gates: Sequence, terms, nparams: int) -> np.ndarray:
+    """d<H>/d theta_p by the parameter-shift rule: every trainable angle here
+    enters as exp(-i theta G / 2) with G^2 = I up to a global phase (RX, RY, RZ,
+    P and each angle of U3), so (E(theta + pi/2) - E(theta - pi/2)) / 2 is the
+    exact derivative; a parameter used by several gates sums their terms."""
+    g = np.zeros(nparams)
+    for p, uses in enumerate(_occurrences(gates, nparams)):
+        for gi, slot in uses:
+            ep = energy(n, _shifted(gates, gi, slot, math.pi / 2), terms)
+            em = energy(n, _shifted(gates, gi, slot, -math.pi / 2), terms)
+            g[p] += 0.5 * (ep - em)
+    return g
+
+
+def finite_diff_grad(n: int, gates: Sequence, terms, nparams: int, h: float = 1e-3) -> np.ndarray:
+    """Central differences (E(theta_p + h) - E(theta_p - h)) / (2h), shifting
+    every gate that uses parameter p together."""
+    g = np.zeros(nparams)
+    for p, uses in enumerate(_occurrences(gates, nparams)):
+        if not uses:
+            continue
+        gp, gm = list(gates), list(gates)
+        for gi, slot in uses:
+            gp = _shifted(gp, gi, slot, h)
+            gm = _shifted(gm, gi, slot, -h)
+        g[p] = (energy(n, gp, terms) - energy(n, gm, terms)) / (2 * h)
+    return g
