@@ -1,0 +1,343 @@
+"""Benchmark: gate-amplitude updates/s of the state-vector hot path at 30 qubits.
+
+One step = set |0...0>, apply the 30-qubit, 40-layer random circuit (U3 on every
+qubit + brickwork CNOT, 1,780 gates, complex64) and read <Z_q> for every qubit.
+updates/s = (gates x 2^n) / step time (every gate counts one pass over the state).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--mode fused|plain]
+                    [--impl ours|reference] [--no-cpu-baseline]
+
+Under torchrun (N > 1) every rank runs its own replica on its own GPU (the
+single-circuit path does not shard); value = all ranks' updates / max time.
+--impl reference times the CPU oracle (complex128, host cores) on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gate-amplitude updates/s and % of HBM roofline at 30 qubits; adjoint grad time"
+UNIT = "gate-amplitude updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="fused", choices=["fused", "plain"])
+    ap.add_argument("--n", type=int, default=30)
+    ap.add_argument("--layers", type=int, default=40)
+    ap.add_argument("--tile-bits", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-gates-per-step", type=int, default=2)
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_2508_15545_gb300 import workloads as W
+    gates = W.random_circuit(args.n, args.layers, W.config_seed(1))
+    cfg = {
+        "workload": "random circuit, %d qubits, %d layers of U3 on every qubit + brickwork CNOT "
+                    "(%d gates), complex64 state from |0...0>, <Z_q> read-out" % (args.n, args.layers, len(gates)),
+        "n_qubits": args.n, "layers": args.layers, "gates": len(gates),
+        "state_bytes": (1 << args.n) * 8,
+        "l2": "inputs larger than L2 (%.1f GiB state vs 129 MB L2)" % ((1 << args.n) * 8 / 2 ** 30),
+        "seed": W.config_seed(1),
+    }
+    return gates, cfg
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2508_15545_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(fn.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_class: str, mode: str):
+    """Per-launch DRAM bytes of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get("%s/%s" % (kernel_class, mode))
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and --impl reference)
+# ----------------------------------------------------------------------------
+def oracle_sample(args, gates, seconds: float, max_gates: int | None = None):
+    """Applies gates of the workload in order to the full 2^n complex128 state
+    with the oracle (one host thread) until `seconds` elapse or `max_gates`
+    are done. Returns (gates applied, elapsed seconds)."""
+    from oracle import oracle
+    psi = oracle.basis(args.n, 0)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        oracle.run(args.n, [gates[done % len(gates)]], psi)
+        done += 1
+        el = time.perf_counter() - t0
+        if (max_gates is not None and done >= max_gates) or (max_gates is None and el >= seconds):
+            return done, el, psi
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    gates, cfg = workload(args)
+    from oracle import oracle
+    psi = oracle.basis(args.n, 0)
+    N = 1 << args.n
+    g = args.ref_gates_per_step
+    pos = 0
+
+    def step():
+        nonlocal pos
+        for _ in range(g):
+            oracle.run(args.n, [gates[pos % len(gates)]], psi)
+            pos += 1
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    ms = el / args.steps * 1e3
+    value = g * N / (ms / 1e3)
+    sample = "%d gates per step of the %d-gate circuit on the full 2^%d complex128 state" % (g, len(gates), args.n)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": cfg,
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                            "host_cores_available": os.cpu_count()},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2508_15545_gb300 import qv
+    gates, cfg = workload(args)
+    mode = qv.QV_MODE_FUSED if args.mode == "fused" else qv.QV_MODE_PLAIN
+    cfg["mode"] = args.mode
+    cfg["parallelism"] = "replicas%d" % world if world > 1 else "single GPU"
+    garr = qv.gates_to_c(gates)
+    ng = len(gates)
+    N = 1 << args.n
+
+    stream = torch.cuda.current_stream(dev)
+    st = qv.StateVector(args.n, qv.QV_C64, stream=stream)
+    h = st.h
+
+    def step():
+        qv.qv_set_basis(h, 0)
+        qv.qv_apply_circuit(h, (garr, ng), mode, args.tile_bits)
+        return qv.qv_expect_z(h)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    barrier()
+    qv.qv_profile(h, timing=False)
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        ez, _ = step()
+    ev1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    stats = qv.qv_profile_read(h)
+    launches = sum(v[0] for v in stats.values())
+
+    # per-class device time: separate timed steps with events around each launch
+    qv.qv_profile(h, timing=True)
+    for _ in range(2):
+        step()
+    tstats = qv.qv_profile_read(h)
+    qv.qv_profile(h, timing=False)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        qv.qv_profile(h, timing=False)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            qv.qv_set_basis(h, 0)
+            qv.qv_apply_circuit(h, gates, mode, args.tile_bits)   # host gate list, marshalled + copied
+            qv.qv_expect_z(h)                                       # D2H of <Z_q>
+        torch.cuda.synchronize(dev)
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        h2d, d2h = qv.qv_transfer_bytes(h)
+        e2e = {"value_s": e2e_s, "h2d": h2d / args.steps, "d2h": d2h / args.steps}
+
+    t = torch.tensor([ms, e2e["value_s"] if e2e else 0.0], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max, e2e_max = float(t[0]), float(t[1])
+
+    updates = ng * N
+    value = world * updates / (ms_max / 1e3)
+    peak, peak_kind = peaks()
+    # dominant kernel class by device time
+    dom = max(tstats.items(), key=lambda kv: kv[1][1])
+    dname, (dl, dms, dbytes) = dom
+    achieved = dbytes / (dms / 1e3) / 1e9 if dms > 0 else None
+    per_launch = dbytes / dl if dl else None
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
+                     "traffic": ncu_traffic(dname, args.mode),
+                     "algorithmic_bytes_per_launch": per_launch,
+                     "avg_launch_ms": dms / dl if dl else None,
+                     "share_of_step": dms / sum(v[1] for v in tstats.values())},
+        "kernel_classes": {k: {"launches": v[0] / 2, "ms": v[1] / 2, "GBps": (v[2] / (v[1] / 1e3) / 1e9) if v[1] else None}
+                           for k, v in tstats.items() if v[0]},
+    }
+    if e2e:
+        out["e2e"] = {"value": world * updates / e2e_max, "unit": UNIT,
+                      "h2d_bytes_per_step": int(e2e["h2d"]), "d2h_bytes_per_step": int(e2e["d2h"])}
+    st.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        done, el, _ = oracle_sample(args, gates, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": done * N / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": "first %d gates of the circuit on the full 2^%d complex128 state, "
+                                         "one host thread, %.1f s" % (done, args.n, el),
+                               "host_cores_available": os.cpu_count()}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

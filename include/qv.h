@@ -1,0 +1,220 @@
+/*
+ * qv.h -- C ABI of libqv.so, a GB300 (sm_103a) state-vector simulator built on
+ * the amplitude-pairing rule of QVecOpt (arXiv 2508.15545).
+ *
+ * Problem statement (Sec. II, Eq. 1-2): an n-qubit state is a dense vector of
+ * 2^n complex amplitudes, 8 bytes each in single precision (QV_C64: float re,
+ * float im) or 16 bytes in double precision (QV_C128: double re, double im),
+ * stored interleaved (re, im) in index order on the GPU. Qubit q is bit q of
+ * the amplitude index (little-endian): a gate on qubit k pairs amplitude i with
+ * amplitude i XOR 2^k (Sec. III-A, Eq. 5).
+ *
+ * Conventions for every entry point:
+ *   - Every call returns a qv_status; QV_OK is 0. On failure qv_last_error()
+ *     returns a message for the calling thread. No call aborts the process or
+ *     traps the GPU; a failed call leaves the state's contents unspecified but
+ *     the handle valid (destroy it or overwrite it).
+ *   - Work is enqueued on the handle's CUDA stream (the one given at creation
+ *     or by qv_set_stream) and the call returns without synchronising, except
+ *     calls that write host memory (qv_get_state, reductions, gradients), which
+ *     synchronise that stream before returning.
+ *   - Host arrays passed in are owned by the caller and only read during the
+ *     call; the library copies gate lists. Host outputs are written before the
+ *     call returns.
+ *   - One handle must not be used from two host threads at once.
+ */
+#ifndef QV_H
+#define QV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qv_state qv_state;   /* opaque handle */
+
+typedef enum { QV_C64 = 0, QV_C128 = 1 } qv_dtype;
+
+typedef enum {
+    QV_OK = 0,
+    QV_ERR_ARG = 1,          /* bad argument: qubit out of range, ctrl == target, NULL, non-finite matrix ... */
+    QV_ERR_OOM = 2,          /* device allocation failed or the state would not fit */
+    QV_ERR_CUDA = 3,         /* a CUDA runtime call failed (message has the CUDA error string) */
+    QV_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up (status word set by a kernel) */
+    QV_ERR_UNSUPPORTED = 5   /* valid request this build does not handle */
+} qv_status;
+
+typedef struct { double re, im; } qv_c128;
+
+/* Gate kinds. Matrices follow OpenQASM: RX/RY/RZ(t) = exp(-i t sigma / 2),
+ * P(l) = diag(1, e^{il}), U3(t,p,l) = [[cos t/2, -e^{il} sin t/2],
+ * [e^{ip} sin t/2, e^{i(p+l)} cos t/2]], H = [[1,1],[1,-1]]/sqrt 2. */
+typedef enum {
+    QV_G_H = 0, QV_G_X = 1, QV_G_Y = 2, QV_G_Z = 3, QV_G_S = 4, QV_G_SDG = 5,
+    QV_G_T = 6, QV_G_TDG = 7, QV_G_RX = 8, QV_G_RY = 9, QV_G_RZ = 10, QV_G_P = 11,
+    QV_G_U3 = 12, QV_G_MATRIX = 13, QV_G_SWAP = 14
+} qv_gate_kind;
+
+/* One gate of a circuit. target: the qubit the 2x2 matrix acts on; target2:
+ * second qubit of QV_G_SWAP (else -1); ctrl: control qubit (the gate acts on
+ * the amplitudes whose control bit is 1) or -1; theta: angles (RX/RY/RZ/P use
+ * theta[0]; U3 uses theta, phi, lambda); param: index of the trainable
+ * parameter behind each angle, or -1 (used by qv_adjoint_grad only);
+ * u: row-major matrix for QV_G_MATRIX (row/column 0 = target bit 0). */
+typedef struct {
+    int32_t kind;
+    int32_t target;
+    int32_t target2;
+    int32_t ctrl;
+    int32_t param[3];
+    int32_t reserved;
+    double  theta[3];
+    qv_c128 u[4];
+} qv_gate;
+
+/* How qv_apply_circuit runs a gate list. */
+typedef enum {
+    QV_MODE_AUTO = 0,    /* fused passes when n >= the tile size, else per gate */
+    QV_MODE_PLAIN = 1,   /* one strided pair-update kernel per gate (Eq. 5 per gate) */
+    QV_MODE_FUSED = 2    /* tiled passes: many gates per HBM round trip */
+} qv_mode;
+
+typedef struct {
+    int32_t mode;        /* qv_mode */
+    int32_t tile_bits;   /* fused: log2 of the tile size in amplitudes (0 = default) */
+    int32_t reserved[6]; /* set to 0 */
+} qv_plan_opts;
+
+/* One Pauli string times a real coefficient: X on the qubits set only in
+ * xmask, Z on those set only in zmask, Y on those set in both. */
+typedef struct {
+    double   coeff;
+    uint64_t xmask;
+    uint64_t zmask;
+} qv_pauli_term;
+
+/* ------------------------------------------------------------------------ */
+/* State lifetime (Sec. II, Eq. 1-2)                                          */
+/* ------------------------------------------------------------------------ */
+
+/* Allocates a 2^n-amplitude state of dtype dt on the current CUDA device
+ * (1 <= n <= 40) and sets it to |0...0> (amplitude 0 = 1) on `cuda_stream`
+ * (a cudaStream_t, NULL = legacy default stream). The library owns the
+ * device buffer. QV_ERR_OOM if it does not fit. */
+qv_status qv_create(int n, qv_dtype dt, void *cuda_stream, qv_state **out);
+
+/* Wraps a caller-owned device buffer of 2^n amplitudes (interleaved re, im;
+ * 16-byte aligned) without copying or initialising it. The buffer must stay
+ * valid until qv_destroy; the library never frees it. */
+qv_status qv_wrap(void *dev_ptr, int n, qv_dtype dt, void *cuda_stream, qv_state **out);
+
+/* Frees the handle (and the device buffer if the library allocated it) after
+ * synchronising its stream. NULL is accepted. */
+qv_status qv_destroy(qv_state *s);
+
+/* Changes the stream later calls enqueue on. */
+qv_status qv_set_stream(qv_state *s, void *cuda_stream);
+
+/* Reports n, dtype and the device pointer of the amplitudes (any may be NULL). */
+qv_status qv_info(const qv_state *s, int *n, qv_dtype *dt, void **dev_ptr);
+
+/* Sets the state to the basis state |j> (amplitude j = 1, all others 0). */
+qv_status qv_set_basis(qv_state *s, uint64_t j);
+
+/* Copies the whole state to / from host memory. `bytes` must equal
+ * 2^n * (8 or 16). qv_get_state synchronises. */
+qv_status qv_get_state(qv_state *s, void *host, size_t bytes);
+qv_status qv_set_state(qv_state *s, const void *host, size_t bytes);
+
+/* ------------------------------------------------------------------------ */
+/* Gates                                                                      */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. 5: (a_i, a_{i^2^t}) <- U (a_i, a_{i^2^t}) for every i with bit t = 0,
+ * one pass over the state. U is row-major (U[0] = U00, U[1] = U01, U[2] = U10,
+ * U[3] = U11), given in double precision and rounded once to the state's
+ * precision. Any 2x2 matrix is accepted (unitarity is not checked); non-finite
+ * entries give QV_ERR_ARG. */
+qv_status qv_apply_1q(qv_state *s, int target, const qv_c128 U[4]);
+
+/* Controlled U: Eq. 5 restricted to the pairs whose bit `ctrl` is 1 (the paper
+ * names CNOT in Sec. II without printing a rule; this is |0><0| (x) I +
+ * |1><1| (x) U). ctrl == target gives QV_ERR_ARG. */
+qv_status qv_apply_controlled(qv_state *s, int ctrl, int target, const qv_c128 U[4]);
+
+/* Applies gates g[0..ng-1] in order (Eq. 3 per gate). The gate list is copied
+ * and validated first; on QV_ERR_ARG nothing has been applied. `opts` may be
+ * NULL (QV_MODE_AUTO). In fused mode the paper's sliding window and block
+ * storage (Sec. III-B/C, Eq. 6-8) become 2^k-amplitude tiles held on chip, and
+ * consecutive gates whose pairs fall inside a tile share one pass over HBM
+ * (Sec. III-E). The result equals per-gate application up to rounding order. */
+qv_status qv_apply_circuit(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_opts *opts);
+
+/* Reorders qubits: bit q of every amplitude index moves to bit perm[q]
+ * (out[pi(i)] = in[i]). perm is a permutation of 0..n-1. In place. */
+qv_status qv_permute_qubits(qv_state *s, const int32_t *perm);
+
+/* ------------------------------------------------------------------------ */
+/* Reductions (not in the paper). Squares and short runs are summed in the   */
+/* state's precision with error-free (two-sum) compensation; everything       */
+/* beyond a thread is summed in FP64 with Neumaier compensation.             */
+/* ------------------------------------------------------------------------ */
+
+/* <psi|psi>. Synchronises. */
+qv_status qv_norm2(qv_state *s, double *out);
+
+/* <Z_q> = sum_i |a_i|^2 (1 - 2 bit_q(i)) for q = 0..n-1 into per_qubit[n]
+ * (may be NULL) and sum_q weights[q] <Z_q> into *total (weights NULL = all 1;
+ * total may be NULL). Synchronises. */
+qv_status qv_expect_z(qv_state *s, const double *weights, double *per_qubit, double *total);
+
+/* <psi|H|psi> for H = sum_t terms[t].coeff * P_t. Synchronises. */
+qv_status qv_expect_pauli(qv_state *s, const qv_pauli_term *terms, size_t nt, double *out);
+
+/* ------------------------------------------------------------------------ */
+/* Instrumentation (not in the paper)                                         */
+/* ------------------------------------------------------------------------ */
+
+/* Kernel classes the library launches. */
+typedef enum {
+    QV_K_BASIS = 0,    /* state set-up */
+    QV_K_PAIR = 1,     /* per-gate pair update (Eq. 5), plain and controlled */
+    QV_K_DIAG = 2,     /* per-gate diagonal gate */
+    QV_K_SWAP = 3,     /* per-gate qubit swap */
+    QV_K_FUSED = 4,    /* tiled multi-gate pass */
+    QV_K_REDUCE = 5,   /* norm / Z reductions */
+    QV_K_PAULI = 6,    /* Pauli-string expectation and H|psi> */
+    QV_K_ADJOINT = 7,  /* adjoint reverse sweep */
+    QV_K_BATCH = 8,    /* batched persistent launch */
+    QV_K_VERIFY = 9,   /* closed-form verification */
+    QV_K_COUNT = 10
+} qv_kernel_class;
+
+typedef struct {
+    uint64_t launches;   /* kernels of this class launched since the last reset */
+    double ms;           /* summed device time (CUDA events around each launch) when timing is on */
+    double bytes;        /* algorithmic HBM bytes: one read and one write of every amplitude the
+                            launches had to change, one read of those they only read */
+} qv_kernel_stat;
+
+/* Resets the handle's counters; with timing != 0 every later launch is
+ * bracketed by CUDA events on the handle's stream (small overhead per launch). */
+qv_status qv_profile(qv_state *s, int timing);
+
+/* Synchronises, then writes min(count, QV_K_COUNT) per-class stats. */
+qv_status qv_profile_read(qv_state *s, qv_kernel_stat *out, int count);
+
+/* Bytes the library copied host->device and device->host since the last
+ * qv_profile reset (gate programs, results; not qv_get/set_state). */
+qv_status qv_transfer_bytes(qv_state *s, uint64_t *h2d, uint64_t *d2h);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *qv_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QV_H */

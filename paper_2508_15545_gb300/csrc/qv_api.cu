@@ -1,0 +1,353 @@
+// C ABI entry points (include/qv.h): handle lifetime, argument checks, gate
+// matrices in FP64, and dispatch to the kernels.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "qv_device.cuh"
+#include "qv_internal.h"
+#include "qv_plan.h"
+
+namespace qv {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+
+qv_status fail(qv_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+qv_status cuda_fail(cudaError_t e, const char *what)
+{
+    const qv_status st = (e == cudaErrorMemoryAllocation) ? QV_ERR_OOM : QV_ERR_CUDA;
+    (void)cudaGetLastError();  // clear a sticky launch error so the handle stays usable
+    return fail(st, "%s: %s", what, cudaGetErrorString(e));
+}
+
+qv_status ensure_scratch(qv_state *s, size_t bytes)
+{
+    if (s->scratch.bytes >= bytes) return QV_OK;
+    if (s->scratch.ptr) {
+        QV_CUDA(cudaStreamSynchronize(s->stream));
+        QV_CUDA(cudaFree(s->scratch.ptr));
+        s->scratch = Scratch{};
+    }
+    const size_t b = std::max<size_t>(bytes, 1 << 20);
+    QV_CUDA(cudaMalloc(&s->scratch.ptr, b));
+    s->scratch.bytes = b;
+    return QV_OK;
+}
+
+qv_status ensure_host_out(qv_state *s, size_t count)
+{
+    if (s->host_out_len >= count) return QV_OK;
+    if (s->host_out) {
+        QV_CUDA(cudaStreamSynchronize(s->stream));
+        QV_CUDA(cudaFreeHost(s->host_out));
+        s->host_out = nullptr;
+        s->host_out_len = 0;
+    }
+    const size_t c = std::max<size_t>(count, 4096);
+    QV_CUDA(cudaMallocHost(&s->host_out, c * sizeof(double)));
+    s->host_out_len = c;
+    return QV_OK;
+}
+
+// ---------------------------------------------------------------- gate matrices
+bool gate_matrix(const qv_gate &g, cd U[4])
+{
+    const double th = g.theta[0], ph = g.theta[1], la = g.theta[2];
+    const double h = 1.0 / std::sqrt(2.0);
+    const cd I(0, 1);
+    auto set = [&](cd a, cd b, cd c, cd d) {
+        U[0] = a; U[1] = b; U[2] = c; U[3] = d;
+        return true;
+    };
+    switch (g.kind) {
+    case QV_G_H: return set(h, h, h, -h);
+    case QV_G_X: return set(0, 1, 1, 0);
+    case QV_G_Y: return set(0, -I, I, 0);
+    case QV_G_Z: return set(1, 0, 0, -1);
+    case QV_G_S: return set(1, 0, 0, I);
+    case QV_G_SDG: return set(1, 0, 0, -I);
+    case QV_G_T: return set(1, 0, 0, cd(h, h));
+    case QV_G_TDG: return set(1, 0, 0, cd(h, -h));
+    case QV_G_RX: return set(std::cos(th / 2), -I * std::sin(th / 2), -I * std::sin(th / 2), std::cos(th / 2));
+    case QV_G_RY: return set(std::cos(th / 2), -std::sin(th / 2), std::sin(th / 2), std::cos(th / 2));
+    case QV_G_RZ: return set(std::polar(1.0, -th / 2), 0, 0, std::polar(1.0, th / 2));
+    case QV_G_P: return set(1, 0, 0, std::polar(1.0, th));
+    case QV_G_U3:
+        return set(std::cos(th / 2), -std::polar(1.0, la) * std::sin(th / 2), std::polar(1.0, ph) * std::sin(th / 2),
+                   std::polar(1.0, ph + la) * std::cos(th / 2));
+    case QV_G_MATRIX:
+        return set(cd(g.u[0].re, g.u[0].im), cd(g.u[1].re, g.u[1].im), cd(g.u[2].re, g.u[2].im),
+                   cd(g.u[3].re, g.u[3].im));
+    default: return false;
+    }
+}
+
+bool is_diagonal(const cd U[4]) { return U[1] == cd(0, 0) && U[2] == cd(0, 0); }
+
+static bool finite(const cd U[4])
+{
+    for (int e = 0; e < 4; ++e)
+        if (!std::isfinite(U[e].real()) || !std::isfinite(U[e].imag())) return false;
+    return true;
+}
+
+qv_status validate_gate(const qv_gate &g, int n, size_t idx)
+{
+    if (g.target < 0 || g.target >= n) return fail(QV_ERR_ARG, "gate %zu: target %d out of range [0, %d)", idx, g.target, n);
+    if (g.kind == QV_G_SWAP) {
+        if (g.target2 < 0 || g.target2 >= n || g.target2 == g.target)
+            return fail(QV_ERR_ARG, "gate %zu: bad swap partner %d", idx, g.target2);
+        if (g.ctrl >= 0) return fail(QV_ERR_UNSUPPORTED, "gate %zu: controlled swap", idx);
+        return QV_OK;
+    }
+    if (g.ctrl >= n || g.ctrl == g.target || g.ctrl < -1)
+        return fail(QV_ERR_ARG, "gate %zu: bad control %d (target %d)", idx, g.ctrl, g.target);
+    cd U[4];
+    if (!gate_matrix(g, U)) return fail(QV_ERR_ARG, "gate %zu: unknown kind %d", idx, g.kind);
+    if (!finite(U)) return fail(QV_ERR_ARG, "gate %zu: non-finite matrix", idx);
+    return QV_OK;
+}
+
+// One gate through the per-gate kernels.
+qv_status apply_gate_plain(qv_state *s, const qv_gate &g)
+{
+    if (g.kind == QV_G_SWAP) return launch_swap(s, g.target, g.target2);
+    cd U[4];
+    gate_matrix(g, U);
+    if (is_diagonal(U)) return launch_diag(s, g.target, g.ctrl, U[0], U[3]);
+    return launch_pair(s, g.target, g.ctrl, U);
+}
+
+}  // namespace qv
+
+using namespace qv;
+
+#define CHECK_HANDLE(s) \
+    if (!(s)) return fail(QV_ERR_ARG, "NULL state handle")
+
+extern "C" {
+
+qv_status qv_wrap(void *dev_ptr, int n, qv_dtype dt, void *cuda_stream, qv_state **out)
+{
+    if (!out) return fail(QV_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!dev_ptr) return fail(QV_ERR_ARG, "device pointer is NULL");
+    if (n < 1 || n > 40) return fail(QV_ERR_ARG, "n = %d outside [1, 40]", n);
+    if (dt != QV_C64 && dt != QV_C128) return fail(QV_ERR_ARG, "bad dtype %d", int(dt));
+    if (reinterpret_cast<uintptr_t>(dev_ptr) % 16) return fail(QV_ERR_ARG, "device pointer not 16-byte aligned");
+    qv_state *s = new qv_state;
+    s->n = n;
+    s->dt = dt;
+    s->amp = dev_ptr;
+    s->owned = false;
+    s->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
+    if (e != cudaSuccess) {
+        delete s;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    *out = s;
+    return QV_OK;
+}
+
+qv_status qv_create(int n, qv_dtype dt, void *cuda_stream, qv_state **out)
+{
+    if (!out) return fail(QV_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > 40) return fail(QV_ERR_ARG, "n = %d outside [1, 40]", n);
+    if (dt != QV_C64 && dt != QV_C128) return fail(QV_ERR_ARG, "bad dtype %d", int(dt));
+    const size_t bytes = (size_t(1) << n) * amp_bytes(dt);
+    size_t free_b = 0, total_b = 0;
+    cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemGetInfo");
+    if (bytes > free_b) return fail(QV_ERR_OOM, "state needs %zu bytes, %zu free", bytes, free_b);
+    void *p = nullptr;
+    e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(state)");
+    qv_status st = qv_wrap(p, n, dt, cuda_stream, out);
+    if (st != QV_OK) {
+        cudaFree(p);
+        return st;
+    }
+    (*out)->owned = true;
+    st = launch_set_basis(*out, 0);
+    if (st != QV_OK) {
+        qv_destroy(*out);
+        *out = nullptr;
+    }
+    return st;
+}
+
+qv_status qv_destroy(qv_state *s)
+{
+    if (!s) return QV_OK;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    plan_cache_release(s);
+    prof_release(s);
+    if (s->scratch.ptr) cudaFree(s->scratch.ptr);
+    if (s->host_out) cudaFreeHost(s->host_out);
+    if (s->owned && s->amp) cudaFree(s->amp);
+    delete s;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return QV_OK;
+}
+
+qv_status qv_set_stream(qv_state *s, void *cuda_stream)
+{
+    CHECK_HANDLE(s);
+    s->stream = static_cast<cudaStream_t>(cuda_stream);
+    return QV_OK;
+}
+
+qv_status qv_info(const qv_state *s, int *n, qv_dtype *dt, void **dev_ptr)
+{
+    CHECK_HANDLE(s);
+    if (n) *n = s->n;
+    if (dt) *dt = s->dt;
+    if (dev_ptr) *dev_ptr = s->amp;
+    return QV_OK;
+}
+
+qv_status qv_set_basis(qv_state *s, uint64_t j)
+{
+    CHECK_HANDLE(s);
+    if (j >= dim(s)) return fail(QV_ERR_ARG, "basis index out of range");
+    return launch_set_basis(s, j);
+}
+
+qv_status qv_get_state(qv_state *s, void *host, size_t bytes)
+{
+    CHECK_HANDLE(s);
+    if (!host) return fail(QV_ERR_ARG, "host is NULL");
+    if (bytes != dim(s) * amp_bytes(s->dt)) return fail(QV_ERR_ARG, "bytes != state size");
+    QV_CUDA(cudaMemcpyAsync(host, s->amp, bytes, cudaMemcpyDeviceToHost, s->stream));
+    QV_CUDA(cudaStreamSynchronize(s->stream));
+    return QV_OK;
+}
+
+qv_status qv_set_state(qv_state *s, const void *host, size_t bytes)
+{
+    CHECK_HANDLE(s);
+    if (!host) return fail(QV_ERR_ARG, "host is NULL");
+    if (bytes != dim(s) * amp_bytes(s->dt)) return fail(QV_ERR_ARG, "bytes != state size");
+    QV_CUDA(cudaMemcpyAsync(s->amp, host, bytes, cudaMemcpyHostToDevice, s->stream));
+    QV_CUDA(cudaStreamSynchronize(s->stream));
+    return QV_OK;
+}
+
+qv_status qv_apply_1q(qv_state *s, int target, const qv_c128 U[4])
+{
+    CHECK_HANDLE(s);
+    if (!U) return fail(QV_ERR_ARG, "U is NULL");
+    qv_gate g{};
+    g.kind = QV_G_MATRIX;
+    g.target = target;
+    g.target2 = -1;
+    g.ctrl = -1;
+    for (int e = 0; e < 4; ++e) g.u[e] = U[e];
+    QV_TRY(validate_gate(g, s->n, 0));
+    cd M[4];
+    gate_matrix(g, M);
+    return launch_pair(s, target, -1, M);
+}
+
+qv_status qv_apply_controlled(qv_state *s, int ctrl, int target, const qv_c128 U[4])
+{
+    CHECK_HANDLE(s);
+    if (!U) return fail(QV_ERR_ARG, "U is NULL");
+    if (ctrl < 0) return fail(QV_ERR_ARG, "control %d out of range", ctrl);
+    qv_gate g{};
+    g.kind = QV_G_MATRIX;
+    g.target = target;
+    g.target2 = -1;
+    g.ctrl = ctrl;
+    for (int e = 0; e < 4; ++e) g.u[e] = U[e];
+    QV_TRY(validate_gate(g, s->n, 0));
+    cd M[4];
+    gate_matrix(g, M);
+    return launch_pair(s, target, ctrl, M);
+}
+
+qv_status qv_apply_circuit(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_opts *opts)
+{
+    CHECK_HANDLE(s);
+    if (ng && !g) return fail(QV_ERR_ARG, "gate list is NULL");
+    for (size_t k = 0; k < ng; ++k) QV_TRY(validate_gate(g[k], s->n, k));
+    const int mode = opts ? opts->mode : QV_MODE_AUTO;
+    if (mode != QV_MODE_AUTO && mode != QV_MODE_PLAIN && mode != QV_MODE_FUSED)
+        return fail(QV_ERR_ARG, "bad mode %d", mode);
+    if (mode == QV_MODE_PLAIN || (mode == QV_MODE_AUTO && !fused_supported(s, opts))) {
+        for (size_t k = 0; k < ng; ++k) QV_TRY(apply_gate_plain(s, g[k]));
+        return QV_OK;
+    }
+    return apply_fused(s, g, ng, opts);
+}
+
+qv_status qv_permute_qubits(qv_state *s, const int32_t *perm)
+{
+    CHECK_HANDLE(s);
+    if (!perm) return fail(QV_ERR_ARG, "perm is NULL");
+    std::vector<int> seen(s->n, 0);
+    for (int q = 0; q < s->n; ++q) {
+        if (perm[q] < 0 || perm[q] >= s->n || seen[perm[q]]++) return fail(QV_ERR_ARG, "not a permutation");
+    }
+    return apply_permutation(s, perm);
+}
+
+qv_status qv_norm2(qv_state *s, double *out)
+{
+    CHECK_HANDLE(s);
+    if (!out) return fail(QV_ERR_ARG, "out is NULL");
+    std::vector<double> z(s->n + 1);
+    QV_TRY(reduce_zsums(s, z.data()));
+    *out = z[0];
+    return QV_OK;
+}
+
+qv_status qv_expect_z(qv_state *s, const double *weights, double *per_qubit, double *total)
+{
+    CHECK_HANDLE(s);
+    std::vector<double> z(s->n + 1);
+    QV_TRY(reduce_zsums(s, z.data()));
+    Neumaier acc;
+    for (int q = 0; q < s->n; ++q) {
+        const double ez = z[0] - 2.0 * z[1 + q];
+        if (per_qubit) per_qubit[q] = ez;
+        acc.add((weights ? weights[q] : 1.0) * ez);
+    }
+    if (total) *total = acc.value();
+    return QV_OK;
+}
+
+qv_status qv_expect_pauli(qv_state *s, const qv_pauli_term *terms, size_t nt, double *out)
+{
+    CHECK_HANDLE(s);
+    if (!out) return fail(QV_ERR_ARG, "out is NULL");
+    if (nt && !terms) return fail(QV_ERR_ARG, "terms is NULL");
+    const uint64_t lim = s->n >= 64 ? ~uint64_t(0) : (uint64_t(1) << s->n) - 1;
+    for (size_t k = 0; k < nt; ++k)
+        if ((terms[k].xmask | terms[k].zmask) & ~lim) return fail(QV_ERR_ARG, "term %zu acts on a qubit >= n", k);
+    return reduce_pauli(s, terms, nt, out);
+}
+
+const char *qv_last_error(void) { return g_err; }
+
+}  // extern "C"

@@ -1,0 +1,124 @@
+// Device-side helpers: index arithmetic and vectorised amplitude access.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qv {
+
+// Insert a 0 at bit position b of x (bits >= b move up by one).
+__host__ __device__ __forceinline__ uint64_t insert_zero(uint64_t x, int b)
+{
+    const uint64_t lo = x & ((uint64_t(1) << b) - 1);
+    return ((x >> b) << (b + 1)) | lo;
+}
+
+// A group of W consecutive amplitudes held as separate re / im registers.
+// Loads and stores use 16-byte vector accesses: C64 packs 2 amplitudes per
+// float4, C128 one per double2. The group start must be W-aligned.
+template <typename R, int W> struct AmpGroup {
+    R re[W], im[W];
+};
+
+template <int W>
+__device__ __forceinline__ void load_group(const float *base, uint64_t idx, AmpGroup<float, W> &g)
+{
+    static_assert(W % 2 == 0, "C64 groups hold pairs of amplitudes");
+    const float4 *p = reinterpret_cast<const float4 *>(base + 2 * idx);
+#pragma unroll
+    for (int v = 0; v < W / 2; ++v) {
+        const float4 x = p[v];
+        g.re[2 * v] = x.x; g.im[2 * v] = x.y; g.re[2 * v + 1] = x.z; g.im[2 * v + 1] = x.w;
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void store_group(float *base, uint64_t idx, const AmpGroup<float, W> &g)
+{
+    float4 *p = reinterpret_cast<float4 *>(base + 2 * idx);
+#pragma unroll
+    for (int v = 0; v < W / 2; ++v)
+        p[v] = make_float4(g.re[2 * v], g.im[2 * v], g.re[2 * v + 1], g.im[2 * v + 1]);
+}
+
+template <int W>
+__device__ __forceinline__ void load_group(const double *base, uint64_t idx, AmpGroup<double, W> &g)
+{
+    const double2 *p = reinterpret_cast<const double2 *>(base + 2 * idx);
+#pragma unroll
+    for (int v = 0; v < W; ++v) {
+        const double2 x = p[v];
+        g.re[v] = x.x; g.im[v] = x.y;
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void store_group(double *base, uint64_t idx, const AmpGroup<double, W> &g)
+{
+    double2 *p = reinterpret_cast<double2 *>(base + 2 * idx);
+#pragma unroll
+    for (int v = 0; v < W; ++v) p[v] = make_double2(g.re[v], g.im[v]);
+}
+
+// 2x2 complex matrix in working precision, row-major.
+template <typename R> struct Mat2 {
+    R r[4], i[4];
+};
+
+// (a, b) <- U (a, b)
+template <typename R>
+__device__ __forceinline__ void apply2(const Mat2<R> &U, R &ar, R &ai, R &br, R &bi)
+{
+    const R xr = ar, xi = ai, yr = br, yi = bi;
+    ar = U.r[0] * xr - U.i[0] * xi + U.r[1] * yr - U.i[1] * yi;
+    ai = U.r[0] * xi + U.i[0] * xr + U.r[1] * yi + U.i[1] * yr;
+    br = U.r[2] * xr - U.i[2] * xi + U.r[3] * yr - U.i[3] * yi;
+    bi = U.r[2] * xi + U.i[2] * xr + U.r[3] * yi + U.i[3] * yr;
+}
+
+// a <- d a
+template <typename R>
+__device__ __forceinline__ void cmul(R dr, R di, R &ar, R &ai)
+{
+    const R xr = ar;
+    ar = dr * xr - di * ai;
+    ai = dr * ai + di * xr;
+}
+
+// Knuth's two-sum: s + e == a + b exactly (round-to-nearest).
+template <typename R>
+__device__ __forceinline__ void two_sum(R a, R b, R &s, R &e)
+{
+    s = a + b;
+    const R bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Running compensated sum in precision R: hi + lo carries the exact sum of
+// everything added so far up to the rounding of lo.
+template <typename R> struct CompSum {
+    R hi = 0, lo = 0;
+    __device__ __forceinline__ void add(R x)
+    {
+        R s, e;
+        two_sum(hi, x, s, e);
+        hi = s;
+        lo += e;
+    }
+    __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
+};
+
+// Neumaier-compensated FP64 accumulator.
+struct Neumaier {
+    double s = 0, c = 0;
+    __host__ __device__ __forceinline__ void add(double x)
+    {
+        const double t = s + x;
+        if (fabs(s) >= fabs(x)) c += (s - t) + x;
+        else c += (x - t) + s;
+        s = t;
+    }
+    __host__ __device__ __forceinline__ double value() const { return s + c; }
+};
+
+}  // namespace qv

@@ -1,0 +1,124 @@
+// Internal declarations shared by the translation units of libqv.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "qv.h"
+
+namespace qv {
+
+using cd = std::complex<double>;
+
+// Per-handle state. The device buffer holds 2^n interleaved (re, im) pairs.
+struct Scratch {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+// Launch counters and optional CUDA-event timing per kernel class.
+struct Prof {
+    bool timing = false;
+    uint64_t launches[QV_K_COUNT] = {};
+    double ms[QV_K_COUNT] = {};
+    double bytes[QV_K_COUNT] = {};
+    struct Pending {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    uint64_t h2d = 0, d2h = 0;
+};
+
+struct PlanCache;  // fused-pass buffers (fused.cu)
+
+}  // namespace qv
+
+struct qv_state {
+    int n = 0;
+    qv_dtype dt = QV_C64;
+    void *amp = nullptr;          // device amplitudes
+    bool owned = false;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    qv::Scratch scratch;          // reduction partials, gate programs
+    double *host_out = nullptr;   // pinned host buffer for reduction results
+    size_t host_out_len = 0;
+    qv::Prof prof;
+    qv::PlanCache *plan = nullptr;
+};
+
+namespace qv {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char *fmt, ...);
+qv_status fail(qv_status st, const char *fmt, ...);
+qv_status cuda_fail(cudaError_t e, const char *what);
+
+#define QV_CUDA(call)                                          \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return ::qv::cuda_fail(e_, #call); \
+    } while (0)
+
+#define QV_TRY(expr)                           \
+    do {                                       \
+        qv_status st_ = (expr);                \
+        if (st_ != QV_OK) return st_;          \
+    } while (0)
+
+// Counts a launch of class `cls` and, when timing is on, records CUDA events
+// around it on the handle's stream.
+void prof_begin(qv_state *s, int cls);
+// Adds algorithmic HBM bytes to class `cls`.
+inline void prof_bytes(qv_state *s, int cls, double b) { s->prof.bytes[cls] += b; }
+void prof_end(qv_state *s, int cls);
+qv_status prof_drain(qv_state *s);
+void prof_release(qv_state *s);
+
+#define QV_LAUNCH(s, cls, ...)                  \
+    do {                                        \
+        ::qv::prof_begin((s), (cls));           \
+        __VA_ARGS__;                            \
+        ::qv::prof_end((s), (cls));             \
+        QV_CUDA(cudaGetLastError());            \
+    } while (0)
+
+// cudaMemcpyAsync on the handle's stream, counted in the transfer totals.
+qv_status copy_h2d(qv_state *s, void *dst, const void *src, size_t bytes);
+qv_status copy_d2h(qv_state *s, void *dst, const void *src, size_t bytes);
+
+inline size_t amp_bytes(qv_dtype dt) { return dt == QV_C64 ? 8 : 16; }
+inline uint64_t dim(const qv_state *s) { return uint64_t(1) << s->n; }
+
+qv_status ensure_scratch(qv_state *s, size_t bytes);
+qv_status ensure_host_out(qv_state *s, size_t count);
+
+// ---------------------------------------------------------------- gates (host)
+// Matrix of a gate in FP64 (row-major). Returns false for kinds without one.
+bool gate_matrix(const qv_gate &g, cd U[4]);
+bool is_diagonal(const cd U[4]);
+
+// ---------------------------------------------------------------- kernels (pair_kernels.cu)
+qv_status launch_set_basis(qv_state *s, uint64_t j);
+// General 2x2 on target t, optional control (ctrl < 0: none).
+qv_status launch_pair(qv_state *s, int t, int ctrl, const cd U[4]);
+// Diagonal diag(d0, d1) on target t, optional control.
+qv_status launch_diag(qv_state *s, int t, int ctrl, cd d0, cd d1);
+qv_status launch_swap(qv_state *s, int a, int b);
+// out[pi(i)] = in[i]; out and in distinct buffers of the same size.
+qv_status launch_permute(qv_state *s, const void *in, void *out, const int32_t *perm);
+
+// ---------------------------------------------------------------- reductions (reduce_kernels.cu)
+// out[0] = sum |a|^2, out[1 + q] = sum over bit q set of |a|^2, q < n.
+qv_status reduce_zsums(qv_state *s, double *out_host);
+// <psi|P|psi> summed over terms.
+qv_status reduce_pauli(qv_state *s, const qv_pauli_term *terms, size_t nt, double *out_host);
+
+}  // namespace qv

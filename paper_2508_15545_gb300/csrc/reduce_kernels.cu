@@ -1,0 +1,288 @@
+// Reductions over the state: norm and per-qubit Z sums, and Pauli-string
+// expectation values. Not part of the paper (which reports no observables);
+// they read the state once and never write it.
+//
+// Precision: |a|^2 and short runs inside a thread are summed in the state's
+// precision with error-free two-sum compensation (hi + lo), so a thread's
+// partial carries about twice the working precision. Partials are combined in
+// FP64 (shuffle trees inside a block, Neumaier-compensated sums across blocks).
+#include <algorithm>
+
+#include "qv_device.cuh"
+#include "qv_internal.h"
+
+namespace qv {
+namespace {
+
+template <typename R> struct Traits;
+template <> struct Traits<float> { static constexpr int W = 4, LOGW = 2; };
+template <> struct Traits<double> { static constexpr int W = 2, LOGW = 1; };
+
+constexpr int kThreads = 256;         // 8 warps, 8 thread-index bits
+constexpr int kSegBits = 14;          // a block reduces 2^14 consecutive amplitudes
+constexpr int kSmallMaxN = 13;        // below this one block reduces the whole state
+constexpr int kParts = kSegBits + 1;  // per block: total, then S_q for q < kSegBits
+
+__device__ __forceinline__ double warp_sum(double x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Sums V values per thread over the block; result valid in thread 0.
+template <int V> __device__ void block_sum(double (&x)[V], double (*smem)[V])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < V; ++v) x[v] = warp_sum(x[v]);
+    if (lane == 0)
+#pragma unroll
+        for (int v = 0; v < V; ++v) smem[warp][v] = x[v];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int v = 0; v < V; ++v) {
+            double s = 0;
+            for (int w = 0; w < kThreads / 32; ++w) s += smem[w][v];
+            x[v] = s;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- small states
+// One block: out[0] = sum |a|^2, out[1+q] = sum_{bit q set} |a|^2.
+template <typename R> __global__ void __launch_bounds__(kThreads) zsum_small_kernel(const R *amp, int n, double *out)
+{
+    __shared__ double smem[kThreads / 32][kSmallMaxN + 1];
+    double x[kSmallMaxN + 1];
+#pragma unroll
+    for (int v = 0; v <= kSmallMaxN; ++v) x[v] = 0;
+    const uint64_t N = uint64_t(1) << n;
+    for (uint64_t i = threadIdx.x; i < N; i += kThreads) {
+        const double re = amp[2 * i], im = amp[2 * i + 1];
+        const double p = re * re + im * im;
+        x[0] += p;
+#pragma unroll
+        for (int q = 0; q < kSmallMaxN; ++q)
+            if (q < n && ((i >> q) & 1)) x[1 + q] += p;
+    }
+    block_sum<kSmallMaxN + 1>(x, smem);
+    if (threadIdx.x == 0)
+        for (int v = 0; v <= n; ++v) out[v] = x[v];
+}
+
+// ---------------------------------------------------------------- segmented
+// Block b reduces amplitudes [b 2^14, (b+1) 2^14). Thread t reads W-groups
+// g = t + 256 v, so index bits split into: element bits [0, LOGW), thread
+// bits [LOGW, LOGW+8), loop bits [LOGW+8, 14). Writes kParts doubles per block.
+template <typename R> __global__ void __launch_bounds__(kThreads) zsum_seg_kernel(const R *__restrict__ amp, double *part)
+{
+    constexpr int W = Traits<R>::W, LOGW = Traits<R>::LOGW;
+    constexpr int TB = 8;                         // thread bits
+    constexpr int VB = kSegBits - LOGW - TB;      // loop bits
+    __shared__ double smem[kThreads / 32][kParts];
+    CompSum<R> tot, eb[LOGW], vb[VB];
+    const uint64_t seg = uint64_t(blockIdx.x) << kSegBits;
+    const int t = threadIdx.x;
+#pragma unroll 4
+    for (int v = 0; v < (1 << VB); ++v) {
+        AmpGroup<R, W> a;
+        load_group(amp, seg + (uint64_t(t) << LOGW) + (uint64_t(v) << (LOGW + TB)), a);
+        R p[W];
+#pragma unroll
+        for (int e = 0; e < W; ++e) p[e] = a.re[e] * a.re[e] + a.im[e] * a.im[e];
+        R w = 0;
+#pragma unroll
+        for (int e = 0; e < W; ++e) w += p[e];
+        tot.add(w);
+#pragma unroll
+        for (int k = 0; k < LOGW; ++k) {
+            R s = 0;
+#pragma unroll
+            for (int e = 0; e < W; ++e)
+                if ((e >> k) & 1) s += p[e];
+            eb[k].add(s);
+        }
+#pragma unroll
+        for (int k = 0; k < VB; ++k)
+            if ((v >> k) & 1) vb[k].add(w);
+    }
+    double x[kParts];
+    const double T = tot.value();
+    x[0] = T;
+#pragma unroll
+    for (int k = 0; k < LOGW; ++k) x[1 + k] = eb[k].value();
+#pragma unroll
+    for (int k = 0; k < TB; ++k) x[1 + LOGW + k] = ((t >> k) & 1) ? T : 0.0;
+#pragma unroll
+    for (int k = 0; k < VB; ++k) x[1 + LOGW + TB + k] = vb[k].value();
+    block_sum<kParts>(x, smem);
+    if (t == 0)
+        for (int v = 0; v < kParts; ++v) part[uint64_t(blockIdx.x) * kParts + v] = x[v];
+}
+
+// Output o = 0: total; o = 1 + q: S_q. For q < 14 sum column 1+q of the
+// partials; for q >= 14 sum the totals of blocks whose bit (q - 14) is set.
+__global__ void __launch_bounds__(kThreads) zsum_combine_kernel(const double *part, uint64_t nblk, double *out)
+{
+    __shared__ double sh_s[kThreads], sh_c[kThreads];
+    const int o = blockIdx.x;
+    Neumaier acc;
+    for (uint64_t b = threadIdx.x; b < nblk; b += kThreads) {
+        if (o <= kSegBits) acc.add(part[b * kParts + o]);
+        else if ((b >> (o - 1 - kSegBits)) & 1) acc.add(part[b * kParts]);
+    }
+    sh_s[threadIdx.x] = acc.s;
+    sh_c[threadIdx.x] = acc.c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Neumaier f;
+        for (int k = 0; k < kThreads; ++k) f.add(sh_s[k]);
+        double c = 0;
+        for (int k = 0; k < kThreads; ++k) c += sh_c[k];
+        out[o] = f.value() + c;
+    }
+}
+
+// ---------------------------------------------------------------- Pauli strings
+// Terms sharing one X mask x: sum_i Re( conj(a_{i^x}) c(i) a_i ) with
+// c(i) = sum_t coeff_t i^{ny_t} (-1)^{popcount(i & z_t)} (complex coefficient
+// kept as re/im). One partial per block.
+constexpr int kMaxTermsPerGroup = 64;
+struct PauliGroup {
+    uint64_t x;
+    int nt;
+    uint64_t z[kMaxTermsPerGroup];
+    double cre[kMaxTermsPerGroup], cim[kMaxTermsPerGroup];
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) pauli_kernel(const R *__restrict__ amp, uint64_t N, const PauliGroup *g,
+                                                         double *part)
+{
+    __shared__ double smem[kThreads / 32][1];
+    __shared__ PauliGroup sg;
+    if (threadIdx.x == 0) sg = *g;
+    __syncthreads();
+    CompSum<R> acc;
+    for (uint64_t i = uint64_t(blockIdx.x) * kThreads + threadIdx.x; i < N; i += uint64_t(gridDim.x) * kThreads) {
+        const uint64_t j = i ^ sg.x;
+        const R ar = amp[2 * i], ai = amp[2 * i + 1];
+        const R br = amp[2 * j], bi = amp[2 * j + 1];
+        // conj(b) a
+        const R pr = br * ar + bi * ai, pi = br * ai - bi * ar;
+        R cr = 0, ci = 0;
+        for (int k = 0; k < sg.nt; ++k) {
+            const R sgn = (__popcll(i & sg.z[k]) & 1) ? R(-1) : R(1);
+            cr += sgn * R(sg.cre[k]);
+            ci += sgn * R(sg.cim[k]);
+        }
+        acc.add(pr * cr - pi * ci);
+    }
+    double x[1] = {acc.value()};
+    block_sum<1>(x, smem);
+    if (threadIdx.x == 0) part[blockIdx.x] = x[0];
+}
+
+__global__ void sum_parts_kernel(const double *part, int np, double *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        Neumaier a;
+        for (int k = 0; k < np; ++k) a.add(part[k]);
+        *out = a.value();
+    }
+}
+
+template <typename R> qv_status zsums_impl(qv_state *s, double *out_host)
+{
+    const int n = s->n;
+    const R *amp = static_cast<const R *>(s->amp);
+    QV_TRY(ensure_host_out(s, n + 1));
+    if (n <= kSmallMaxN) {
+        QV_TRY(ensure_scratch(s, sizeof(double) * (n + 1)));
+        double *out = static_cast<double *>(s->scratch.ptr);
+        prof_bytes(s, QV_K_REDUCE, double(dim(s)) * 2 * sizeof(R));
+        QV_LAUNCH(s, QV_K_REDUCE, zsum_small_kernel<R><<<1, kThreads, 0, s->stream>>>(amp, n, out));
+        QV_TRY(copy_d2h(s, s->host_out, out, sizeof(double) * (n + 1)));
+    } else {
+        const uint64_t nblk = dim(s) >> kSegBits;
+        const size_t part_bytes = sizeof(double) * nblk * kParts;
+        QV_TRY(ensure_scratch(s, part_bytes + sizeof(double) * (n + 1)));
+        double *part = static_cast<double *>(s->scratch.ptr);
+        double *out = part + nblk * kParts;
+        prof_bytes(s, QV_K_REDUCE, double(dim(s)) * 2 * sizeof(R));
+        QV_LAUNCH(s, QV_K_REDUCE, zsum_seg_kernel<R><<<unsigned(nblk), kThreads, 0, s->stream>>>(amp, part));
+        QV_LAUNCH(s, QV_K_REDUCE, zsum_combine_kernel<<<n + 1, kThreads, 0, s->stream>>>(part, nblk, out));
+        QV_TRY(copy_d2h(s, s->host_out, out, sizeof(double) * (n + 1)));
+    }
+    QV_CUDA(cudaStreamSynchronize(s->stream));
+    std::copy(s->host_out, s->host_out + n + 1, out_host);
+    return QV_OK;
+}
+
+template <typename R> qv_status pauli_impl(qv_state *s, const qv_pauli_term *terms, size_t nt, double *out_host)
+{
+    // Group terms by X mask.
+    std::vector<PauliGroup> groups;
+    for (size_t k = 0; k < nt; ++k) {
+        const uint64_t x = terms[k].xmask, z = terms[k].zmask;
+        const int ny = __builtin_popcountll(x & z);
+        // coeff * i^ny
+        static const double pr[4] = {1, 0, -1, 0}, pi[4] = {0, 1, 0, -1};
+        const double cre = terms[k].coeff * pr[ny & 3], cim = terms[k].coeff * pi[ny & 3];
+        PauliGroup *g = nullptr;
+        for (auto &gg : groups)
+            if (gg.x == x && gg.nt < kMaxTermsPerGroup) { g = &gg; break; }
+        if (!g) {
+            groups.emplace_back();
+            g = &groups.back();
+            g->x = x;
+            g->nt = 0;
+        }
+        g->z[g->nt] = z;
+        g->cre[g->nt] = cre;
+        g->cim[g->nt] = cim;
+        g->nt++;
+    }
+    const unsigned grid = unsigned(std::min<uint64_t>((dim(s) + kThreads - 1) / kThreads, uint64_t(s->num_sms) * 4));
+    const size_t ng = groups.size();
+    const size_t bytes = ng * sizeof(PauliGroup) + sizeof(double) * (ng * grid + ng + 1);
+    QV_TRY(ensure_scratch(s, bytes));
+    QV_TRY(ensure_host_out(s, ng + 1));
+    char *base = static_cast<char *>(s->scratch.ptr);
+    PauliGroup *dg = reinterpret_cast<PauliGroup *>(base);
+    double *part = reinterpret_cast<double *>(base + ng * sizeof(PauliGroup));
+    double *res = part + ng * grid;
+    if (ng == 0) {
+        *out_host = 0;
+        return QV_OK;
+    }
+    QV_TRY(copy_h2d(s, dg, groups.data(), ng * sizeof(PauliGroup)));
+    const R *amp = static_cast<const R *>(s->amp);
+    for (size_t k = 0; k < ng; ++k) {
+        prof_bytes(s, QV_K_PAULI, double(dim(s)) * 2 * sizeof(R));
+        QV_LAUNCH(s, QV_K_PAULI,
+                  pauli_kernel<R><<<grid, kThreads, 0, s->stream>>>(amp, dim(s), dg + k, part + k * grid));
+        QV_LAUNCH(s, QV_K_PAULI, sum_parts_kernel<<<1, 32, 0, s->stream>>>(part + k * grid, int(grid), res + k));
+    }
+    QV_TRY(copy_d2h(s, s->host_out, res, sizeof(double) * ng));
+    QV_CUDA(cudaStreamSynchronize(s->stream));
+    Neumaier tot;
+    for (size_t k = 0; k < ng; ++k) tot.add(s->host_out[k]);
+    *out_host = tot.value();
+    return QV_OK;
+}
+
+}  // namespace
+
+qv_status reduce_zsums(qv_state *s, double *out_host)
+{
+    return s->dt == QV_C64 ? zsums_impl<float>(s, out_host) : zsums_impl<double>(s, out_host);
+}
+
+qv_status reduce_pauli(qv_state *s, const qv_pauli_term *terms, size_t nt, double *out_host)
+{
+    return s->dt == QV_C64 ? pauli_impl<float>(s, terms, nt, out_host) : pauli_impl<double>(s, terms, nt, out_host);
+}
+
+}  // namespace qv

@@ -1,0 +1,327 @@
+"""ctypes binding of libqv.so (include/qv.h). Function names match the C ABI;
+this module only marshals arguments. Device memory and streams may come from
+PyTorch (``StateVector`` wraps a torch tensor with ``qv_wrap``).
+
+Importing raises if libqv.so has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Iterable, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libqv.so")
+
+QV_C64, QV_C128 = 0, 1
+QV_OK, QV_ERR_ARG, QV_ERR_OOM, QV_ERR_CUDA, QV_ERR_TIMEOUT, QV_ERR_UNSUPPORTED = range(6)
+QV_MODE_AUTO, QV_MODE_PLAIN, QV_MODE_FUSED = 0, 1, 2
+STATUS_NAMES = {0: "QV_OK", 1: "QV_ERR_ARG", 2: "QV_ERR_OOM", 3: "QV_ERR_CUDA",
+                4: "QV_ERR_TIMEOUT", 5: "QV_ERR_UNSUPPORTED"}
+KIND = {"h": 0, "x": 1, "y": 2, "z": 3, "s": 4, "sdg": 5, "t": 6, "tdg": 7,
+        "rx": 8, "ry": 9, "rz": 10, "p": 11, "u3": 12, "matrix": 13, "swap": 14}
+
+
+class QvError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class qv_c128(ctypes.Structure):
+    _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double)]
+
+
+class qv_gate(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("target", ctypes.c_int32), ("target2", ctypes.c_int32),
+                ("ctrl", ctypes.c_int32), ("param", ctypes.c_int32 * 3), ("reserved", ctypes.c_int32),
+                ("theta", ctypes.c_double * 3), ("u", qv_c128 * 4)]
+
+
+class qv_plan_opts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("tile_bits", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+
+
+class qv_kernel_stat(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+KERNEL_CLASSES = ("basis", "pair", "diag", "swap", "fused", "reduce", "pauli", "adjoint", "batch", "verify")
+
+
+class qv_pauli_term(ctypes.Structure):
+    _fields_ = [("coeff", ctypes.c_double), ("xmask", ctypes.c_uint64), ("zmask", ctypes.c_uint64)]
+
+
+_H = ctypes.c_void_p  # qv_state*
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libqv.so not built (run paper_2508_15545_gb300.build.build()); "
+                          "there is no CPU fallback")
+    L = ctypes.CDLL(LIB_PATH)
+    st = ctypes.c_int
+    P = ctypes.c_void_p
+    sig = {
+        "qv_create": [ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(_H)],
+        "qv_wrap": [P, ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(_H)],
+        "qv_destroy": [_H],
+        "qv_set_stream": [_H, P],
+        "qv_info": [_H, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(P)],
+        "qv_set_basis": [_H, ctypes.c_uint64],
+        "qv_get_state": [_H, P, ctypes.c_size_t],
+        "qv_set_state": [_H, P, ctypes.c_size_t],
+        "qv_apply_1q": [_H, ctypes.c_int, ctypes.POINTER(qv_c128)],
+        "qv_apply_controlled": [_H, ctypes.c_int, ctypes.c_int, ctypes.POINTER(qv_c128)],
+        "qv_apply_circuit": [_H, ctypes.POINTER(qv_gate), ctypes.c_size_t, ctypes.POINTER(qv_plan_opts)],
+        "qv_permute_qubits": [_H, ctypes.POINTER(ctypes.c_int32)],
+        "qv_norm2": [_H, ctypes.POINTER(ctypes.c_double)],
+        "qv_expect_z": [_H, P, P, ctypes.POINTER(ctypes.c_double)],
+        "qv_expect_pauli": [_H, ctypes.POINTER(qv_pauli_term), ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)],
+        "qv_profile": [_H, ctypes.c_int],
+        "qv_profile_read": [_H, ctypes.POINTER(qv_kernel_stat), ctypes.c_int],
+        "qv_transfer_bytes": [_H, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = st
+    L.qv_last_error.argtypes = []
+    L.qv_last_error.restype = ctypes.c_char_p
+    return L
+
+
+lib = _load()
+
+
+def _check(status: int):
+    if status != QV_OK:
+        raise QvError(status, lib.qv_last_error().decode(errors="replace"))
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    """Accepts None, an int (cudaStream_t) or a torch.cuda.Stream."""
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+# ----------------------------------------------------------------------------
+# marshalling helpers
+# ----------------------------------------------------------------------------
+def c128_array(U) -> ctypes.Array:
+    U = np.asarray(U, dtype=np.complex128).reshape(4)
+    arr = (qv_c128 * 4)()
+    for e in range(4):
+        arr[e].re = U[e].real
+        arr[e].im = U[e].imag
+    return arr
+
+
+def gates_to_c(gates: Sequence) -> ctypes.Array:
+    """workloads.Gate records -> qv_gate[]."""
+    arr = (qv_gate * max(1, len(gates)))()
+    for i, g in enumerate(gates):
+        o = arr[i]
+        o.kind = KIND[g.kind]
+        o.target = g.target
+        o.target2 = g.target2
+        o.ctrl = g.ctrl
+        for e in range(3):
+            o.param[e] = g.param[e]
+            o.theta[e] = g.theta[e]
+        if g.matrix is not None:
+            for e, z in enumerate(g.matrix):
+                o.u[e].re = complex(z).real
+                o.u[e].im = complex(z).imag
+    return arr
+
+
+def terms_to_c(terms: Sequence[Tuple[float, int, int]]) -> ctypes.Array:
+    arr = (qv_pauli_term * max(1, len(terms)))()
+    for i, (c, x, z) in enumerate(terms):
+        arr[i].coeff = c
+        arr[i].xmask = x
+        arr[i].zmask = z
+    return arr
+
+
+def plan_opts(mode: int = QV_MODE_AUTO, tile_bits: int = 0) -> qv_plan_opts:
+    o = qv_plan_opts()
+    o.mode = mode
+    o.tile_bits = tile_bits
+    return o
+
+
+# ----------------------------------------------------------------------------
+# C ABI, one Python function per entry point
+# ----------------------------------------------------------------------------
+def qv_create(n: int, dtype: int = QV_C64, stream=None) -> int:
+    h = _H()
+    _check(lib.qv_create(n, dtype, _stream_ptr(stream), ctypes.byref(h)))
+    return h.value
+
+
+def qv_wrap(dev_ptr: int, n: int, dtype: int = QV_C64, stream=None) -> int:
+    h = _H()
+    _check(lib.qv_wrap(dev_ptr, n, dtype, _stream_ptr(stream), ctypes.byref(h)))
+    return h.value
+
+
+def qv_destroy(h: int):
+    _check(lib.qv_destroy(h))
+
+
+def qv_set_stream(h: int, stream):
+    _check(lib.qv_set_stream(h, _stream_ptr(stream)))
+
+
+def qv_info(h: int):
+    n, dt, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_void_p()
+    _check(lib.qv_info(h, ctypes.byref(n), ctypes.byref(dt), ctypes.byref(p)))
+    return n.value, dt.value, p.value
+
+
+def qv_set_basis(h: int, j: int):
+    _check(lib.qv_set_basis(h, j))
+
+
+def qv_get_state(h: int) -> np.ndarray:
+    n, dt, _ = qv_info(h)
+    out = np.empty(1 << n, dtype=np.complex64 if dt == QV_C64 else np.complex128)
+    _check(lib.qv_get_state(h, out.ctypes.data, out.nbytes))
+    return out
+
+
+def qv_set_state(h: int, psi: np.ndarray):
+    n, dt, _ = qv_info(h)
+    a = np.ascontiguousarray(psi, dtype=np.complex64 if dt == QV_C64 else np.complex128)
+    _check(lib.qv_set_state(h, a.ctypes.data, a.nbytes))
+
+
+def qv_apply_1q(h: int, target: int, U):
+    _check(lib.qv_apply_1q(h, target, c128_array(U)))
+
+
+def qv_apply_controlled(h: int, ctrl: int, target: int, U):
+    _check(lib.qv_apply_controlled(h, ctrl, target, c128_array(U)))
+
+
+def qv_apply_circuit(h: int, gates, mode: int = QV_MODE_AUTO, tile_bits: int = 0):
+    """``gates``: a sequence of workloads.Gate or a prebuilt qv_gate array
+    (``gates_to_c``) with its length as ``(array, count)``."""
+    if isinstance(gates, tuple) and len(gates) == 2 and isinstance(gates[1], int):
+        arr, ng = gates
+    else:
+        arr, ng = gates_to_c(gates), len(gates)
+    opts = plan_opts(mode, tile_bits)
+    _check(lib.qv_apply_circuit(h, arr, ng, ctypes.byref(opts)))
+
+
+def qv_permute_qubits(h: int, perm: Sequence[int]):
+    arr = (ctypes.c_int32 * max(1, len(perm)))(*perm)
+    _check(lib.qv_permute_qubits(h, arr))
+
+
+def qv_norm2(h: int) -> float:
+    out = ctypes.c_double()
+    _check(lib.qv_norm2(h, ctypes.byref(out)))
+    return out.value
+
+
+def qv_expect_z(h: int, weights: Optional[Sequence[float]] = None):
+    """Returns (per-qubit <Z_q> as numpy array, weighted total)."""
+    n, _, _ = qv_info(h)
+    per = np.zeros(n)
+    tot = ctypes.c_double()
+    w = None
+    if weights is not None:
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        if w.size != n:
+            raise ValueError("weights must have n entries")
+    _check(lib.qv_expect_z(h, None if w is None else w.ctypes.data, per.ctypes.data, ctypes.byref(tot)))
+    return per, tot.value
+
+
+def qv_expect_pauli(h: int, terms: Sequence[Tuple[float, int, int]]) -> float:
+    out = ctypes.c_double()
+    _check(lib.qv_expect_pauli(h, terms_to_c(terms), len(terms), ctypes.byref(out)))
+    return out.value
+
+
+def qv_profile(h: int, timing: bool = False):
+    _check(lib.qv_profile(h, 1 if timing else 0))
+
+
+def qv_profile_read(h: int) -> dict:
+    """{class name: (launches, device ms, algorithmic bytes)}"""
+    arr = (qv_kernel_stat * len(KERNEL_CLASSES))()
+    _check(lib.qv_profile_read(h, arr, len(KERNEL_CLASSES)))
+    return {name: (int(arr[k].launches), float(arr[k].ms), float(arr[k].bytes))
+            for k, name in enumerate(KERNEL_CLASSES)}
+
+
+def qv_transfer_bytes(h: int):
+    a, b = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib.qv_transfer_bytes(h, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def qv_last_error() -> str:
+    return lib.qv_last_error().decode(errors="replace")
+
+
+# ----------------------------------------------------------------------------
+# torch-owned state
+# ----------------------------------------------------------------------------
+class StateVector:
+    """A 2^n state held in a torch CUDA tensor and driven through the C ABI on
+    torch's current stream (or ``stream``)."""
+
+    def __init__(self, n: int, dtype: int = QV_C64, stream=None, basis: int = 0):
+        import torch
+        self.n = n
+        self.dtype = dtype
+        tdt = torch.complex64 if dtype == QV_C64 else torch.complex128
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.tensor = torch.empty(1 << n, dtype=tdt, device="cuda")
+        self.h = qv_wrap(self.tensor.data_ptr(), n, dtype, self.stream)
+        qv_set_basis(self.h, basis)
+
+    def close(self):
+        if self.h:
+            qv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def apply(self, gates, mode: int = QV_MODE_AUTO, tile_bits: int = 0):
+        qv_apply_circuit(self.h, gates, mode, tile_bits)
+        return self
+
+    def numpy(self) -> np.ndarray:
+        return qv_get_state(self.h)
+
+    def expect_z(self, weights=None):
+        return qv_expect_z(self.h, weights)
+
+    def expect_pauli(self, terms) -> float:
+        return qv_expect_pauli(self.h, terms)
+
+    def norm2(self) -> float:
+        return qv_norm2(self.h)

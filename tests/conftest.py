@@ -18,3 +18,20 @@ def orc():
     from oracle import oracle as O
     O.lib()
     return O
+
+
+@pytest.fixture(scope="session")
+def qvlib():
+    """libqv.so (built if stale) through the ctypes binding."""
+    from paper_2508_15545_gb300 import build
+    build.build()
+    from paper_2508_15545_gb300 import qv
+    return qv
+
+
+@pytest.fixture(scope="session")
+def cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
