@@ -173,6 +173,32 @@ qv_status qv_expect_z(qv_state *s, const double *weights, double *per_qubit, dou
 /* <psi|H|psi> for H = sum_t terms[t].coeff * P_t. Synchronises. */
 qv_status qv_expect_pauli(qv_state *s, const qv_pauli_term *terms, size_t nt, double *out);
 
+/* Allocation-free Z sums (the paper has no counterpart; this exists for
+ * callers that cannot allocate device memory). Some callers cannot call
+ * cudaMalloc at the point where they need a result: code recording a CUDA
+ * graph, where a cudaMalloc/cudaFree would not be captured and may
+ * synchronise the device; latency-critical loops, where those calls block
+ * and can serialise unrelated streams; processes whose device memory is
+ * carved out by a pool or quota they do not own. This call needs no handle
+ * and allocates nothing: it runs the same kernels as qv_expect_z on a
+ * caller-owned state and writes, on the device,
+ *     dev_out[0]     = sum_i |a_i|^2
+ *     dev_out[1 + q] = sum over i with bit q set of |a_i|^2   (q < n)
+ * (so <Z_q> = dev_out[0] - 2 dev_out[1 + q]). dev_amp: 2^n amplitudes of dtype
+ * dt, 16-byte aligned; dev_out: n + 1 doubles of device memory, 8-byte
+ * aligned, owned by the caller. Work is enqueued on cuda_stream; the call
+ * returns without synchronising and without any host<->device copy.
+ * Limit: 1 <= n <= 30 (QV_ERR_ARG beyond). The partial sums of states with
+ * n >= 14 live in one fixed 7,864,320-byte device array inside the library,
+ * present on every device that loads it until the process exits. The first
+ * call on a device looks that array's address up (cudaGetSymbolAddress, which
+ * may load the library's device code); make that first call before any stream
+ * capture. Every call shares the array, so calls that can overlap on the GPU
+ * (different streams without ordering) race and give wrong sums; calls on one
+ * stream are safe. Nothing in the array needs to start at zero: every call
+ * overwrites the part it reads. */
+qv_status qv_zsums_noalloc(const void *dev_amp, int n, qv_dtype dt, void *cuda_stream, double *dev_out);
+
 /* ------------------------------------------------------------------------ */
 /* Instrumentation (not in the paper)                                         */
 /* ------------------------------------------------------------------------ */

@@ -7,6 +7,7 @@
 // partial carries about twice the working precision. Partials are combined in
 // FP64 (shuffle trees inside a block, Neumaier-compensated sums across blocks).
 #include <algorithm>
+#include <mutex>
 
 #include "qv_device.cuh"
 #include "qv_internal.h"
@@ -285,4 +286,71 @@ qv_status reduce_pauli(qv_state *s, const qv_pauli_term *terms, size_t nt, doubl
     return s->dt == QV_C64 ? pauli_impl<float>(s, terms, nt, out_host) : pauli_impl<double>(s, terms, nt, out_host);
 }
 
+// ---------------------------------------------------------------- allocation-free Z sums
+// Same kernels as reduce_zsums, but the per-block partials live in a fixed
+// device array owned by this library instead of per-handle cudaMalloc'd
+// scratch. Sized for states up to kStaticMaxN qubits: 2^(30-14) blocks x 15
+// doubles = 7,864,320 bytes, held on every device that loads the library.
+constexpr int kStaticMaxN = 30;
+constexpr uint64_t kStaticBlocks = uint64_t(1) << (kStaticMaxN - kSegBits);
+__device__ __align__(256) double g_zsum_static[kStaticBlocks * kParts];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+double *g_static_ptr[kMaxDevices] = {};
+
+// Device address of g_zsum_static on the current device, looked up once per
+// device (host code cannot use the symbol itself as a device pointer).
+qv_status static_scratch(double **out)
+{
+    int dev = 0;
+    QV_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(QV_ERR_UNSUPPORTED, "device ordinal %d too large", dev);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        QV_CUDA(cudaGetSymbolAddress(&p, g_zsum_static));
+        g_static_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_static_ptr[dev];
+    return QV_OK;
+}
+
+template <typename R>
+qv_status zsums_noalloc_impl(const void *dev_amp, int n, cudaStream_t stream, double *dev_out)
+{
+    const R *amp = static_cast<const R *>(dev_amp);
+    if (n <= kSmallMaxN) {
+        zsum_small_kernel<R><<<1, kThreads, 0, stream>>>(amp, n, dev_out);
+        QV_CUDA(cudaGetLastError());
+        return QV_OK;
+    }
+    double *part = nullptr;
+    QV_TRY(static_scratch(&part));
+    const uint64_t nblk = (uint64_t(1) << n) >> kSegBits;
+    // Every block writes all kParts of its partials, so nothing needs clearing.
+    zsum_seg_kernel<R><<<unsigned(nblk), kThreads, 0, stream>>>(amp, part);
+    QV_CUDA(cudaGetLastError());
+    zsum_combine_kernel<<<n + 1, kThreads, 0, stream>>>(part, nblk, dev_out);
+    QV_CUDA(cudaGetLastError());
+    return QV_OK;
+}
+}  // namespace
+
 }  // namespace qv
+
+extern "C" qv_status qv_zsums_noalloc(const void *dev_amp, int n, qv_dtype dt, void *cuda_stream, double *dev_out)
+{
+    using namespace qv;
+    if (!dev_amp || !dev_out) return fail(QV_ERR_ARG, "NULL device pointer");
+    if (reinterpret_cast<uintptr_t>(dev_amp) % 16) return fail(QV_ERR_ARG, "amplitudes not 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(dev_out) % 8) return fail(QV_ERR_ARG, "output not 8-byte aligned");
+    if (dt != QV_C64 && dt != QV_C128) return fail(QV_ERR_ARG, "bad dtype %d", int(dt));
+    if (n < 1 || n > kStaticMaxN)
+        return fail(QV_ERR_ARG, "qv_zsums_noalloc: n = %d outside [1, %d] (its fixed scratch holds the partials of "
+                                "at most 2^%d amplitudes)", n, kStaticMaxN, kStaticMaxN);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    return dt == QV_C64 ? zsums_noalloc_impl<float>(dev_amp, n, st, dev_out)
+                        : zsums_noalloc_impl<double>(dev_amp, n, st, dev_out);
+}

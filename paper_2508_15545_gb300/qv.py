@@ -81,6 +81,7 @@ def _load():
         "qv_norm2": [_H, ctypes.POINTER(ctypes.c_double)],
         "qv_expect_z": [_H, P, P, ctypes.POINTER(ctypes.c_double)],
         "qv_expect_pauli": [_H, ctypes.POINTER(qv_pauli_term), ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)],
+        "qv_zsums_noalloc": [P, ctypes.c_int, ctypes.c_int, P, P],
         "qv_profile": [_H, ctypes.c_int],
         "qv_profile_read": [_H, ctypes.POINTER(qv_kernel_stat), ctypes.c_int],
         "qv_transfer_bytes": [_H, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
@@ -252,6 +253,12 @@ def qv_expect_pauli(h: int, terms: Sequence[Tuple[float, int, int]]) -> float:
     out = ctypes.c_double()
     _check(lib.qv_expect_pauli(h, terms_to_c(terms), len(terms), ctypes.byref(out)))
     return out.value
+
+
+def qv_zsums_noalloc(dev_amp: int, n: int, dtype: int, stream, dev_out: int):
+    """Allocation-free Z sums into the caller's device buffer of n + 1 doubles
+    (see include/qv.h); asynchronous on ``stream``."""
+    _check(lib.qv_zsums_noalloc(dev_amp, n, dtype, _stream_ptr(stream), dev_out))
 
 
 def qv_profile(h: int, timing: bool = False):
