@@ -228,6 +228,9 @@ def run_ours(args):
     cfg["parallelism"] = "replicas%d" % world if world > 1 else "single GPU"
     garr = qv.gates_to_c(gates)
     ng = len(gates)
+    if mode == qv.QV_MODE_FUSED:
+        cfg["plan"] = qv.qv_plan_info(args.n, qv.QV_C64, (garr, ng), args.tile_bits)
+        cfg["tile_bits"] = args.tile_bits or min(args.n, 12)
     N = 1 << args.n
 
     stream = torch.cuda.current_stream(dev)

@@ -152,6 +152,12 @@ qv_status qv_apply_controlled(qv_state *s, int ctrl, int target, const qv_c128 U
  * (Sec. III-E). The result equals per-gate application up to rounding order. */
 qv_status qv_apply_circuit(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_opts *opts);
 
+/* Plans g[0..ng) for an n-qubit state of dtype dt as qv_apply_circuit would in
+ * QV_MODE_FUSED, without touching a GPU, and reports out[0] = HBM passes,
+ * out[1] = on-chip stages, out[2] = shared-memory transposes, out[3] = on-chip
+ * operations. Host only. */
+qv_status qv_plan_info(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t out[4]);
+
 /* Reorders qubits: bit q of every amplitude index moves to bit perm[q]
  * (out[pi(i)] = in[i]). perm is a permutation of 0..n-1. In place. */
 qv_status qv_permute_qubits(qv_state *s, const int32_t *perm);

@@ -54,13 +54,14 @@ def _compile(src: str, obj: str, extra) -> str:
 
 def build(force: bool = False, debug: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
     hdrs = _headers()
     extra = ["-DQV_DEBUG=1"] if debug else []
     jobs = []
     objs = []
     for src in srcs:
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + (".dbg.o" if debug else ".o"))
+        stem = os.path.splitext(os.path.basename(src))[0]
+        obj = os.path.join(BUILD, stem + (".dbg.o" if debug else ".o"))
         objs.append(obj)
         if force or _stale(obj, [src] + hdrs + [__file__]):
             jobs.append((src, obj))

@@ -78,6 +78,8 @@ def _load():
         "qv_apply_controlled": [_H, ctypes.c_int, ctypes.c_int, ctypes.POINTER(qv_c128)],
         "qv_apply_circuit": [_H, ctypes.POINTER(qv_gate), ctypes.c_size_t, ctypes.POINTER(qv_plan_opts)],
         "qv_permute_qubits": [_H, ctypes.POINTER(ctypes.c_int32)],
+        "qv_plan_info": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(qv_gate), ctypes.c_size_t,
+                         ctypes.POINTER(qv_plan_opts), ctypes.POINTER(ctypes.c_int32)],
         "qv_norm2": [_H, ctypes.POINTER(ctypes.c_double)],
         "qv_expect_z": [_H, P, P, ctypes.POINTER(ctypes.c_double)],
         "qv_expect_pauli": [_H, ctypes.POINTER(qv_pauli_term), ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)],
@@ -222,6 +224,18 @@ def qv_apply_circuit(h: int, gates, mode: int = QV_MODE_AUTO, tile_bits: int = 0
         arr, ng = gates_to_c(gates), len(gates)
     opts = plan_opts(mode, tile_bits)
     _check(lib.qv_apply_circuit(h, arr, ng, ctypes.byref(opts)))
+
+
+def qv_plan_info(n: int, dtype: int, gates, tile_bits: int = 0) -> dict:
+    """Fused-mode plan of ``gates`` (host only): passes, stages, transposes, ops."""
+    if isinstance(gates, tuple) and len(gates) == 2 and isinstance(gates[1], int):
+        arr, ng = gates
+    else:
+        arr, ng = gates_to_c(gates), len(gates)
+    out = (ctypes.c_int32 * 4)()
+    opts = plan_opts(QV_MODE_FUSED, tile_bits)
+    _check(lib.qv_plan_info(n, dtype, arr, ng, ctypes.byref(opts), out))
+    return {"passes": out[0], "stages": out[1], "transposes": out[2], "ops": out[3]}
 
 
 def qv_permute_qubits(h: int, perm: Sequence[int]):

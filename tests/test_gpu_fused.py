@@ -1,0 +1,121 @@
+"""Parity of the fused tiled passes (planner + on-chip kernel) against the CPU
+oracle and against the per-gate kernels, through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2508_15545_gb300 import workloads as W
+from paper_2508_15545_gb300.workloads import Gate
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-5, 1: 1e-12}
+
+
+def dist(a, b):
+    return float(np.linalg.norm(a.astype(np.complex128) - b))
+
+
+def run_gpu(qv, n, dtype, gates, psi=None, mode=2, tile_bits=0, basis=0):
+    h = qv.qv_create(n, dtype)
+    try:
+        if psi is not None:
+            qv.qv_set_state(h, psi)
+        else:
+            qv.qv_set_basis(h, basis)
+        qv.qv_apply_circuit(h, gates, mode=mode, tile_bits=tile_bits)
+        return qv.qv_get_state(h)
+    finally:
+        qv.qv_destroy(h)
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("n,k", [(10, 10), (11, 10), (11, 11), (12, 12), (13, 10), (13, 12), (16, 11), (17, 12)])
+def test_random_gate_kinds_fused(qvlib, orc, cuda, dtype, n, k):
+    """Every gate kind, random controls (inside and outside the tile), swaps."""
+    qv = qvlib
+    gates = W.random_gate_list(n, 200, seed=1000 * n + k, ctrl_prob=0.4)
+    psi = W.random_state(n, 31 * n + k)
+    got = run_gpu(qv, n, dtype, gates, psi=psi, tile_bits=k)
+    want = orc.run(n, gates, psi.copy())
+    assert dist(got, want) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_random_circuit_16q_fused(qvlib, orc, cuda, dtype):
+    qv = qvlib
+    n = 16
+    gates = W.random_circuit(n, 20, W.config_seed(0))
+    want = orc.run(n, gates)
+    for k in (10, 11, 12):
+        got = run_gpu(qv, n, dtype, gates, tile_bits=k)
+        assert dist(got, want) <= TOL[dtype], k
+
+
+@pytest.mark.parametrize("n", [10, 12, 15])
+def test_qft_closed_form_fused(qvlib, cuda, n):
+    qv = qvlib
+    N = 1 << n
+    gates = W.qft_circuit(n)
+    for j in (1, N - 1, (3 * N) // 7):
+        k = np.arange(N)
+        want = np.exp(2j * np.pi * ((j * k) % N) / N) / math.sqrt(N)
+        for dtype in (0, 1):
+            got = run_gpu(qv, n, dtype, gates, basis=j)
+            assert dist(got, want) <= (1e-5 if dtype == 0 else 1e-12)
+
+
+def test_ansatz_fused(qvlib, orc, cuda):
+    qv = qvlib
+    n = 14
+    gates, _ = W.ansatz_circuit(n, 6, W.config_seed(2, 3))
+    want = orc.run(n, gates)
+    got = run_gpu(qv, n, 0, gates)
+    assert dist(got, want) <= 1e-5
+
+
+def test_ghz_fused(qvlib, cuda):
+    qv = qvlib
+    n = 20
+    got = run_gpu(qv, n, 0, W.ghz_circuit(n))
+    assert abs(got[0] - 1 / math.sqrt(2)) < 1e-6 and abs(got[-1] - 1 / math.sqrt(2)) < 1e-6
+    assert np.sum(np.abs(got[1:-1])) == 0
+
+
+@pytest.mark.parametrize("n", [10, 13, 18])
+def test_permute_qubits_fused(qvlib, orc, cuda, n):
+    qv = qvlib
+    rng = W.SplitMix64(n + 1)
+    psi = W.random_state(n, 4)
+    for _ in range(3):
+        perm = [int(x) for x in np.argsort(rng.uniform(n))]
+        h = qv.qv_create(n, 1)
+        qv.qv_set_state(h, psi)
+        qv.qv_permute_qubits(h, perm)
+        got = qv.qv_get_state(h)
+        qv.qv_destroy(h)
+        assert dist(got, orc.permute(psi, perm)) <= 1e-14
+
+
+def test_fused_equals_plain_22q(qvlib, orc, cuda):
+    """Same seeded circuit through both GPU paths and the oracle at 22 qubits."""
+    qv = qvlib
+    n = 22
+    gates = W.random_circuit(n, 8, seed=77)
+    fused = run_gpu(qv, n, 0, gates, mode=qv.QV_MODE_FUSED)
+    plain = run_gpu(qv, n, 0, gates, mode=qv.QV_MODE_PLAIN)
+    want = orc.run(n, gates)
+    assert dist(fused, want) <= 1e-5
+    assert dist(plain, want) <= 1e-5
+    assert dist(fused, plain.astype(np.complex128)) <= 1e-5
+
+
+def test_fused_reports_bad_tile_bits(qvlib, cuda):
+    qv = qvlib
+    h = qv.qv_create(11, 0)
+    with pytest.raises(qv.QvError):
+        qv.qv_apply_circuit(h, [Gate("h", 0)], mode=qv.QV_MODE_FUSED, tile_bits=13)
+    with pytest.raises(qv.QvError):
+        qv.qv_apply_circuit(h, [Gate("h", 0)], mode=qv.QV_MODE_FUSED, tile_bits=12)   # > n
+    qv.qv_destroy(h)
