@@ -81,10 +81,14 @@ typedef enum {
     QV_MODE_FUSED = 2    /* tiled passes: many gates per HBM round trip */
 } qv_mode;
 
+/* qv_plan_opts.flags */
+#define QV_PLAN_NO_FUSION 1  /* fused mode: one on-chip operation per gate (no 2x2 products) */
+
 typedef struct {
     int32_t mode;        /* qv_mode */
     int32_t tile_bits;   /* fused: log2 of the tile size in amplitudes (0 = default) */
-    int32_t reserved[6]; /* set to 0 */
+    int32_t flags;       /* QV_PLAN_* bits */
+    int32_t reserved[5]; /* set to 0 */
 } qv_plan_opts;
 
 /* One Pauli string times a real coefficient: X on the qubits set only in

@@ -2,16 +2,17 @@
 #include "planner.h"
 
 #include <algorithm>
-#include <cstdio>
 
 namespace qv {
 namespace plan {
 
 namespace {
 
-constexpr int kMaxOpsPerPass = 384;
-constexpr int kMaxStagesPerPass = 48;
+constexpr int kMaxOpsPerPass = 160;
+constexpr int kMaxStagesPerPass = 40;
 constexpr int kLookahead = 96;  // gates scanned when ranking candidate tile qubits
+
+using cd = std::complex<double>;
 
 // Tile qubits a gate needs: the target of a non-diagonal 2x2, both qubits of a
 // SWAP; diagonal gates and controls need none (their bits may lie outside).
@@ -36,14 +37,13 @@ inline int qubits(const PGate &g, int out[3])
 
 // In-order scan with blocking: a gate is taken when none of its qubits is
 // blocked by an earlier gate left behind and `ok(g)` holds; a gate left behind
-// blocks all of its qubits. Returns the taken gate indices (into `rem`).
+// blocks all of its qubits. Returns the number taken; `taken` gets indices into rem.
 template <typename Ok>
-int scan(const std::vector<PGate> &gates, const std::vector<int> &rem, int n, Ok ok, std::vector<int> *taken,
-         int limit = 1 << 30)
+int scan(const std::vector<PGate> &gates, const std::vector<int> &rem, int n, Ok ok, std::vector<int> *taken)
 {
     std::vector<char> blocked(n, 0);
-    int cnt = 0, seen = 0;
-    for (size_t r = 0; r < rem.size() && seen < limit; ++r, ++seen) {
+    int cnt = 0;
+    for (size_t r = 0; r < rem.size(); ++r) {
         const PGate &g = gates[rem[r]];
         int qs[3];
         const int nq = qubits(g, qs);
@@ -61,7 +61,6 @@ int scan(const std::vector<PGate> &gates, const std::vector<int> &rem, int n, Ok
 
 struct LayoutState {
     int k;
-    bool lane0;      // 8-byte amplitudes: two per 16-byte access, tile position 0 on register bit 0
     Layout L;
     int nq() const { return k - kRegBits; }
     int reg_of(int pos) const
@@ -78,25 +77,23 @@ struct LayoutState {
     }
 };
 
-bool is_canonical(const Layout &L, int k, bool lane0)
+// Layout constraints. With pin0, register bit 3 is tile position 0 and the
+// shared-memory word index is l >> 1; otherwise the word index is l.
+inline int lane_first(bool pin0) { return pin0 ? 1 : 0; }
+
+bool is_canonical(const Layout &L, bool pin0)
 {
-    if (lane0) {
-        if (L.P[0] != 0) return false;
-        for (int b = 0; b < 5; ++b)
-            if (L.Q[b] != b + 1) return false;
-    } else {
-        for (int b = 0; b < 5; ++b)
-            if (L.Q[b] != b) return false;
-    }
-    (void)k;
+    if (pin0 && L.P[3] != 0) return false;
+    for (int b = 0; b < 5; ++b)
+        if (L.Q[b] != b + lane_first(pin0)) return false;
     return true;
 }
 
-// Builds a layout with register positions `regs`. Thread bits: the first few
-// lanes take positions of distinct residue classes so the swizzled
-// shared-memory transpose stays free of bank conflicts (8-byte amplitudes: a
-// half warp, 4 lane bits, residues mod 4; 16-byte: a quarter warp, mod 3).
-Layout make_layout(int k, bool lane0, const int regs[kRegBits])
+// Thread bits for register positions `regs`: the first lanes take positions
+// whose word-index bit falls in distinct residue classes, so the swizzled
+// transpose is free of bank conflicts (8-byte words: a half warp = 4 lane
+// bits, residues mod 4; 16-byte words: a quarter warp = 3 lane bits, mod 3).
+Layout make_layout(int k, bool pin0, const int regs[kRegBits])
 {
     Layout L;
     for (int j = 0; j < kRegBits; ++j) L.P[j] = int8_t(regs[j]);
@@ -106,12 +103,12 @@ Layout make_layout(int k, bool lane0, const int regs[kRegBits])
         for (int j = 0; j < kRegBits; ++j) r |= regs[j] == p;
         if (!r) rest.push_back(p);
     }
-    const int nl = lane0 ? 4 : 3, mod = lane0 ? 4 : 3;
+    const int nl = pin0 ? 4 : 3, mod = pin0 ? 4 : 3, sh = pin0 ? 1 : 0;
     std::vector<int> q;
     std::vector<char> used(rest.size(), 0);
     for (int res = 0; res < mod && int(q.size()) < nl; ++res)
         for (size_t i = 0; i < rest.size(); ++i)
-            if (!used[i] && rest[i] % mod == res) {
+            if (!used[i] && (rest[i] - sh) % mod == res) {
                 q.push_back(rest[i]);
                 used[i] = 1;
                 break;
@@ -123,21 +120,21 @@ Layout make_layout(int k, bool lane0, const int regs[kRegBits])
     return L;
 }
 
-Layout canonical_layout(int k, bool lane0, const int extra[kRegBits])
+// Load/store layout: lanes on positions f..f+4 (f = 1 with pin0, else 0);
+// register bits on `extra` (positions >= f + 5) plus position 0 with pin0.
+Layout canonical_layout(int k, bool pin0, const int extra[kRegBits])
 {
-    // 8-byte: P = {0, e0, e1, e2} (e >= 6), Q = 1..5 then the rest ascending.
-    // 16-byte: P = {e0..e3} (e >= 5), Q = 0..4 then the rest ascending.
     Layout L;
     int regs[kRegBits];
-    if (lane0) {
-        regs[0] = 0;
-        for (int j = 1; j < kRegBits; ++j) regs[j] = extra[j - 1];
+    if (pin0) {
+        for (int j = 0; j < 3; ++j) regs[j] = extra[j];
+        regs[3] = 0;
     } else {
         for (int j = 0; j < kRegBits; ++j) regs[j] = extra[j];
     }
     for (int j = 0; j < kRegBits; ++j) L.P[j] = int8_t(regs[j]);
     int b = 0;
-    const int first = lane0 ? 1 : 0;
+    const int first = lane_first(pin0);
     for (int p = first; p < first + 5; ++p) L.Q[b++] = int8_t(p);
     for (int p = 0; p < k; ++p) {
         bool used = (p >= first && p < first + 5);
@@ -146,6 +143,13 @@ Layout canonical_layout(int k, bool lane0, const int extra[kRegBits])
     }
     for (; b < kMaxK - kRegBits; ++b) L.Q[b] = -1;
     return L;
+}
+
+void matmul(const cd A[4], const cd B[4], cd out[4])  // out = A B
+{
+    const cd r0 = A[0] * B[0] + A[1] * B[2], r1 = A[0] * B[1] + A[1] * B[3];
+    const cd r2 = A[2] * B[0] + A[3] * B[2], r3 = A[2] * B[1] + A[3] * B[3];
+    out[0] = r0; out[1] = r1; out[2] = r2; out[3] = r3;
 }
 
 }  // namespace
@@ -157,8 +161,8 @@ int classify(const std::complex<double> U[4])
     return G_GEN;
 }
 
-bool make_plan(int n, int k, bool lane0, const std::vector<PGate> &gates, std::vector<Pass> &out, PlanStats &stats,
-               std::string &err)
+bool make_plan(int n, int k, bool pin0, bool fuse, const std::vector<PGate> &gates, std::vector<Pass> &out,
+               PlanStats &stats, std::string &err)
 {
     out.clear();
     stats = PlanStats{};
@@ -167,29 +171,55 @@ bool make_plan(int n, int k, bool lane0, const std::vector<PGate> &gates, std::v
         return false;
     }
     const int nh = k - kChunkBits;
+    if (pin0) {
+        // Qubit 0 never leaves register bit 3, so a SWAP touching it cannot be
+        // a relabeling: expand it into CNOT(0->x) CNOT(x->0) CNOT(0->x).
+        bool any = false;
+        for (const PGate &g : gates) any |= g.cls == G_SWAP && (g.t == 0 || g.t2 == 0);
+        if (any) {
+            std::vector<PGate> ex;
+            ex.reserve(gates.size() + 8);
+            for (const PGate &g : gates) {
+                if (g.cls == G_SWAP && (g.t == 0 || g.t2 == 0)) {
+                    const int x = g.t == 0 ? g.t2 : g.t;
+                    PGate c{};
+                    c.cls = G_X;
+                    c.t2 = -1;
+                    c.U[0] = 0.0; c.U[1] = 1.0; c.U[2] = 1.0; c.U[3] = 0.0;
+                    c.t = x; c.c = 0; ex.push_back(c);
+                    c.t = 0; c.c = x; ex.push_back(c);
+                    c.t = x; c.c = 0; ex.push_back(c);
+                } else {
+                    ex.push_back(g);
+                }
+            }
+            return make_plan(n, k, pin0, fuse, ex, out, stats, err);
+        }
+    }
     std::vector<int> rem(gates.size());
     for (size_t i = 0; i < gates.size(); ++i) rem[i] = int(i);
+    const int first_free = pin0 ? 6 : 5;  // lowest position a canonical register bit may take
 
     while (!rem.empty()) {
         // ---- choose the tile's high qubits greedily
         std::vector<char> inS(n, 0);
         for (int q = 0; q < kChunkBits; ++q) inS[q] = 1;
+        auto fits = [&](const PGate &g) {
+            int need[2];
+            const int nn = needs(g, need);
+            for (int i = 0; i < nn; ++i)
+                if (!inS[need[i]]) return false;
+            return true;
+        };
         for (int step = 0; step < nh; ++step) {
             int best = -1;
             long long best_score = -1;
             for (int q = kChunkBits; q < n; ++q) {
                 if (inS[q]) continue;
                 inS[q] = 1;
-                const int cnt = scan(gates, rem, n, [&](const PGate &g) {
-                    int need[2];
-                    const int nn = needs(g, need);
-                    for (int i = 0; i < nn; ++i)
-                        if (!inS[need[i]]) return false;
-                    return true;
-                }, nullptr);
+                const int cnt = scan(gates, rem, n, fits, nullptr);
                 inS[q] = 0;
-                // tie-break: gates needing q soon
-                int soon = 0;
+                int soon = 0;  // tie-break: gates needing q soon
                 for (size_t r = 0; r < rem.size() && r < size_t(kLookahead); ++r) {
                     int need[2];
                     const int nn = needs(gates[rem[r]], need);
@@ -205,8 +235,7 @@ bool make_plan(int n, int k, bool lane0, const std::vector<PGate> &gates, std::v
         }
         Pass P;
         P.k = k;
-        int pos_of[64];
-        for (int q = 0; q < n; ++q) pos_of[q] = -1;
+        std::vector<int> pos_of(n, -1);
         for (int q = 0; q < kChunkBits; ++q) pos_of[q] = q;
         {
             int j = 0;
@@ -217,8 +246,7 @@ bool make_plan(int n, int k, bool lane0, const std::vector<PGate> &gates, std::v
                     ++j;
                 }
         }
-        // tile id bits -> runs of physical bits outside the tile
-        {
+        {  // tile id bits -> runs of physical bits outside the tile
             int src = 0;
             for (int q = 0; q < n;) {
                 if (inS[q]) {
@@ -235,36 +263,25 @@ bool make_plan(int n, int k, bool lane0, const std::vector<PGate> &gates, std::v
                 q += w;
             }
         }
-        // ---- gates of this pass (in order with blocking)
         std::vector<int> taken;
-        scan(gates, rem, n, [&](const PGate &g) {
-            int need[2];
-            const int nn = needs(g, need);
-            for (int i = 0; i < nn; ++i)
-                if (!inS[need[i]]) return false;
-            return true;
-        }, &taken);
+        scan(gates, rem, n, fits, &taken);
         if (taken.empty()) {
             err = "planner made no progress";
             return false;
         }
-        std::vector<int> pg;  // gate indices of this pass, in order
+        std::vector<int> pg;
         for (int r : taken) pg.push_back(rem[r]);
 
         // ---- stages: run gates whose target is a register bit; transpose otherwise
-        LayoutState ls{k, lane0, {}};
-        auto frontier_targets = [&](const std::vector<int> &left, std::vector<int> &pos, bool restrict_canon) {
-            // targets (tile positions) of non-diagonal gates in frontier order, then any later ones
+        LayoutState ls{k, {}};
+        // targets (tile positions) of non-diagonal gates in frontier order, then later ones
+        auto frontier_targets = [&](const std::vector<int> &left, std::vector<int> &pos, int lo, int want) {
             std::vector<char> blocked(n, 0);
             auto consider = [&](int p) {
-                if (p < 0) return;
-                if (restrict_canon) {
-                    if (lane0 && p < 6) return;
-                    if (!lane0 && p < 5) return;
-                }
+                if (p < lo || (pin0 && p == 0)) return;
                 if (std::find(pos.begin(), pos.end(), p) == pos.end()) pos.push_back(p);
             };
-            for (int pass2 = 0; pass2 < 2 && int(pos.size()) < kRegBits; ++pass2) {
+            for (int round = 0; round < 2 && int(pos.size()) < want; ++round) {
                 std::fill(blocked.begin(), blocked.end(), 0);
                 for (int gi : left) {
                     const PGate &g = gates[gi];
@@ -272,58 +289,106 @@ bool make_plan(int n, int k, bool lane0, const std::vector<PGate> &gates, std::v
                     const int nq = qubits(g, qs);
                     bool blk = false;
                     for (int i = 0; i < nq; ++i) blk |= blocked[qs[i]] != 0;
-                    if ((g.cls == G_GEN || g.cls == G_X) && (pass2 == 1 || !blk)) consider(pos_of[g.t]);
+                    if ((g.cls == G_GEN || g.cls == G_X) && (round == 1 || !blk) && pos_of[g.t] >= 0)
+                        consider(pos_of[g.t]);
                     for (int i = 0; i < nq; ++i) blocked[qs[i]] = 1;
-                    if (int(pos.size()) >= kRegBits) break;
+                    if (int(pos.size()) >= want) break;
                 }
             }
         };
+        const int nfree = pin0 ? 3 : 4;  // register bits the planner chooses
         std::vector<int> left = pg;
         std::vector<Stage> stages;
         std::vector<Op> ops;
         {
             std::vector<int> pos;
-            frontier_targets(left, pos, true);
-            const int lo = lane0 ? 6 : 5;
-            for (int p = k - 1; p >= lo && int(pos.size()) < kRegBits; --p)
+            frontier_targets(left, pos, first_free, nfree);
+            for (int p = k - 1; p >= first_free && int(pos.size()) < nfree; --p)
                 if (std::find(pos.begin(), pos.end(), p) == pos.end()) pos.push_back(p);
             int extra[kRegBits] = {0, 0, 0, 0};
-            for (int j = 0; j < (lane0 ? 3 : 4); ++j) extra[j] = pos[j];
-            ls.L = canonical_layout(k, lane0, extra);
+            for (int j = 0; j < nfree; ++j) extra[j] = pos[j];
+            ls.L = canonical_layout(k, pin0, extra);
         }
         Stage cur{ls.L, ls.L, 0, 0};
-        auto emit = [&](const PGate &g) {
-            Op o{};
-            o.treg = o.creg = -1;
-            if (g.c >= 0) {
-                const int pc = pos_of[g.c];
-                if (pc < 0) o.cext = uint64_t(1) << g.c;
-                else if (ls.reg_of(pc) >= 0) o.creg = int8_t(ls.reg_of(pc));
-                else o.cthr = 1u << ls.thr_of(pc);
-            }
-            if (g.cls == G_DIAG) {
-                o.type = OP_DIAG;
-                const int pt = pos_of[g.t];
-                if (pt < 0) o.text = uint64_t(1) << g.t;
-                else if (ls.reg_of(pt) >= 0) o.treg = int8_t(ls.reg_of(pt));
-                else o.tthr = 1u << ls.thr_of(pt);
-                o.m[0] = g.U[0].real(); o.m[1] = g.U[0].imag();
-                o.m[2] = g.U[3].real(); o.m[3] = g.U[3].imag();
-            } else {
-                o.type = g.cls == G_X ? OP_X : OP_GEN;
-                o.treg = int8_t(ls.reg_of(pos_of[g.t]));
-                for (int e = 0; e < 4; ++e) {
-                    o.m[2 * e] = g.U[e].real();
-                    o.m[2 * e + 1] = g.U[e].imag();
+
+        // ---- gate fusion bookkeeping (reset at every layout change)
+        std::vector<int> open_op(n, -1);   // op open for fusion on this target qubit
+        std::vector<int> op_sel, op_time;  // per op: select qubit, gate time it was created
+        std::vector<int> last_mod(n, -1);  // gate time of the last non-diagonal gate per qubit
+        int gtime = 0;
+        auto close_all = [&]() { std::fill(open_op.begin(), open_op.end(), -1); };
+        auto coord = [&](int q, int8_t &reg, uint32_t &thr, uint64_t &ext) {
+            const int p = pos_of[q];
+            if (p < 0) ext = uint64_t(1) << q;
+            else if (ls.reg_of(p) >= 0) reg = int8_t(ls.reg_of(p));
+            else thr = 1u << ls.thr_of(p);
+        };
+        auto process = [&](const PGate &g) {
+            const int t = g.t, c = g.c;
+            const bool nondiag = g.cls != G_DIAG;
+            const int o = fuse ? open_op[t] : -1;
+            bool fused = false;
+            if (o >= 0) {
+                Op &op = ops[o];
+                const int so = op_sel[o];
+                if (c < 0) {
+                    for (int s = 0; s < 2; ++s) {
+                        if (s == 0 && op.m0id) {
+                            for (int e = 0; e < 4; ++e) op.M[0][e] = g.U[e];
+                        } else {
+                            matmul(g.U, op.M[s], op.M[s]);
+                        }
+                    }
+                    op.m0id = 0;
+                    fused = true;
+                } else if ((so < 0 || so == c) && last_mod[c] < op_time[o]) {
+                    if (so < 0) {
+                        for (int e = 0; e < 4; ++e) op.M[1][e] = op.M[0][e];
+                        coord(c, op.sreg, op.sthr, op.sext);
+                        op_sel[o] = c;
+                    }
+                    matmul(g.U, op.M[1], op.M[1]);
+                    fused = true;
+                }
+                if (fused) {
+                    // X or diagonal ops absorbing anything but diagonals become general
+                    // 2x2 ops (a non-diagonal gate on t is only run when t is a register bit)
+                    if (nondiag || op.type != OP_DIAG) op.type = OP_GEN;
+                } else {
+                    open_op[t] = -1;
                 }
             }
-            ops.push_back(o);
+            if (!fused) {
+                Op op{};
+                op.treg = op.sreg = -1;
+                op.type = g.cls == G_DIAG ? OP_DIAG : g.cls == G_X ? OP_X : OP_GEN;
+                if (op.type == OP_DIAG) coord(t, op.treg, op.tthr, op.text);
+                else op.treg = int8_t(ls.reg_of(pos_of[t]));
+                const cd I[4] = {1.0, 0.0, 0.0, 1.0};
+                for (int e = 0; e < 4; ++e) {
+                    op.M[0][e] = c >= 0 ? I[e] : g.U[e];
+                    op.M[1][e] = g.U[e];
+                }
+                op.m0id = c >= 0 ? 1 : 0;
+                if (c >= 0) coord(c, op.sreg, op.sthr, op.sext);
+                open_op[t] = int(ops.size());
+                op_sel.push_back(c);
+                op_time.push_back(gtime);
+                ops.push_back(op);
+            }
+            if (nondiag) {
+                last_mod[t] = gtime;
+                for (int q = 0; q < n; ++q)
+                    if (open_op[q] >= 0 && op_sel[open_op[q]] == t) open_op[q] = -1;
+            }
+            if (c >= 0) open_op[c] = -1;
+            ++gtime;
         };
+
         while (!left.empty()) {
             // run every executable gate in order (with blocking)
             std::vector<int> still;
             std::vector<char> blocked(n, 0);
-            int ran = 0;
             for (int gi : left) {
                 const PGate &g = gates[gi];
                 int qs[3];
@@ -342,10 +407,10 @@ bool make_plan(int n, int k, bool lane0, const std::vector<PGate> &gates, std::v
                             ls.L.P[j] = int8_t(ls.L.P[j] == a ? b : ls.L.P[j] == b ? a : ls.L.P[j]);
                         for (int q = 0; q < ls.nq(); ++q)
                             ls.L.Q[q] = int8_t(ls.L.Q[q] == a ? b : ls.L.Q[q] == b ? a : ls.L.Q[q]);
+                        close_all();
                     } else {
-                        emit(g);
+                        process(g);
                     }
-                    ++ran;
                 } else {
                     still.push_back(gi);
                     for (int i = 0; i < nq; ++i) blocked[qs[i]] = 1;
@@ -353,50 +418,47 @@ bool make_plan(int n, int k, bool lane0, const std::vector<PGate> &gates, std::v
             }
             left.swap(still);
             if (left.empty()) break;
-            (void)ran;
-            if (int(ops.size()) >= kMaxOpsPerPass || int(stages.size()) + 2 >= kMaxStagesPerPass) {
-                // pass is full: give the rest back to later passes
-                break;
+            if (int(ops.size()) >= kMaxOpsPerPass || int(stages.size()) + 2 >= kMaxStagesPerPass) break;
+            // the first gate left needs a register bit it lacks: new register set
+            cur.out = ls.L;
+            cur.op_end = int(ops.size());
+            stages.push_back(cur);
+            std::vector<int> pos;
+            frontier_targets(left, pos, 0, nfree);
+            for (int j = 0; j < kRegBits && int(pos.size()) < nfree; ++j) {
+                const int p = ls.L.P[j];
+                if (!(pin0 && p == 0) && std::find(pos.begin(), pos.end(), p) == pos.end()) pos.push_back(p);
             }
-            {
-                // the first gate left needs a register bit it lacks: new register set
-                cur.out = ls.L;
-                cur.op_end = int(ops.size());
-                stages.push_back(cur);
-                std::vector<int> pos;
-                frontier_targets(left, pos, false);
-                for (int j = 0; j < kRegBits && int(pos.size()) < kRegBits; ++j)
-                    if (std::find(pos.begin(), pos.end(), ls.L.P[j]) == pos.end()) pos.push_back(ls.L.P[j]);
-                int regs[kRegBits];
-                for (int j = 0; j < kRegBits; ++j) regs[j] = pos[j];
-                ls.L = make_layout(k, lane0, regs);
-                cur = Stage{ls.L, ls.L, int(ops.size()), int(ops.size())};
-            }
+            int regs[kRegBits];
+            for (int j = 0; j < nfree; ++j) regs[j] = pos[j];
+            if (pin0) regs[3] = 0;
+            ls.L = make_layout(k, pin0, regs);
+            cur = Stage{ls.L, ls.L, int(ops.size()), int(ops.size())};
+            close_all();
         }
         cur.out = ls.L;
         cur.op_end = int(ops.size());
         stages.push_back(cur);
-        if (!is_canonical(ls.L, k, lane0)) {
+        if (!is_canonical(ls.L, pin0)) {
             int extra[kRegBits];
             int ne = 0;
-            const int lo = lane0 ? 6 : 5;
-            for (int j = 0; j < kRegBits && ne < kRegBits; ++j)
-                if (ls.L.P[j] >= lo) extra[ne++] = ls.L.P[j];
-            for (int p = k - 1; p >= lo && ne < kRegBits; --p) {
+            for (int j = 0; j < kRegBits && ne < nfree; ++j)
+                if (ls.L.P[j] >= first_free) extra[ne++] = ls.L.P[j];
+            for (int p = k - 1; p >= first_free && ne < nfree; --p) {
                 bool have = false;
                 for (int e = 0; e < ne; ++e) have |= extra[e] == p;
                 if (!have) extra[ne++] = p;
             }
-            Layout C = canonical_layout(k, lane0, extra);
+            Layout C = canonical_layout(k, pin0, extra);
             stages.push_back(Stage{C, C, int(ops.size()), int(ops.size())});
         }
-        // gates handed to this pass but not run go back to the front of `rem`
-        std::vector<char> ran_mask(gates.size(), 0);
-        for (int gi : pg) ran_mask[gi] = 1;
-        for (int gi : left) ran_mask[gi] = 0;
+        // gates of this pass that did not run go back to `rem`, in order
+        std::vector<char> done(gates.size(), 0);
+        for (int gi : pg) done[gi] = 1;
+        for (int gi : left) done[gi] = 0;
         std::vector<int> nrem;
         for (int gi : rem)
-            if (!ran_mask[gi]) nrem.push_back(gi);
+            if (!done[gi]) nrem.push_back(gi);
         P.ngates = int(pg.size() - left.size());
         P.stages = std::move(stages);
         P.ops = std::move(ops);

@@ -44,18 +44,22 @@ struct PGate {
 
 enum OpType : int8_t { OP_GEN = 0, OP_X = 1, OP_DIAG = 2 };
 
-// One on-chip operation in the coordinates of the current layout.
+// One on-chip operation in the coordinates of the layout of its stage. It
+// applies M[s] to the target qubit, where s is the value of one "select" bit
+// (a register bit, a thread-index bit, a physical qubit outside the tile, or
+// none: s = 0). A controlled gate is M[0] = I, M[1] = U (m0id = 1); the
+// planner multiplies later gates on the same target into an open op (both
+// branches, or only the s = 1 branch for a gate controlled by the select bit).
 struct Op {
-    int8_t type;      // OpType
-    int8_t treg;      // target register bit (GEN, X, DIAG on a register bit), else -1
-    int8_t creg;      // control register bit, else -1
-    int8_t pad0;
-    uint32_t cthr;    // thread-index bits that must all be 1 (controls on thread bits)
-    uint32_t tthr;    // DIAG: thread-index bit selecting d1
-    uint32_t pad1;
-    uint64_t cext;    // physical bits outside the tile that must all be 1
-    uint64_t text;    // DIAG: physical bit outside the tile selecting d1
-    double m[8];      // GEN/X: U00 U01 U10 U11 (re, im); DIAG: d0, d1 (re, im)
+    int8_t type;      // OpType: GEN (any 2x2), X (the bit flip, unfused), DIAG (diagonal)
+    int8_t treg;      // target register bit (GEN, X; DIAG with a register target), else -1
+    int8_t sreg;      // select register bit, else -1
+    int8_t m0id;      // M[0] is the identity
+    uint32_t sthr;    // select = this thread-index bit (0: none)
+    uint32_t tthr;    // DIAG: target on this thread-index bit (0: none)
+    uint64_t sext;    // select = this physical qubit outside the tile (0: none)
+    uint64_t text;    // DIAG: target physical qubit outside the tile (0: none)
+    std::complex<double> M[2][4];   // row-major 2x2 for s = 0 / 1 (DIAG: entries [0], [3])
 };
 
 struct Layout {
@@ -85,11 +89,15 @@ struct PlanStats {
 };
 
 // Plans gates[0..ng) for an n-qubit state with tiles of 2^k amplitudes
-// (kMinK <= k <= min(kMaxK, n)). `canonical_lane0` selects the load/store
-// layout: true for 8-byte amplitudes (register bit 0 = tile position 0, lanes =
-// positions 1..5, two amplitudes per 16-byte access), false for 16-byte ones
-// (lanes = positions 0..4). Returns false with `err` set on failure.
-bool make_plan(int n, int k, bool canonical_lane0, const std::vector<PGate> &gates, std::vector<Pass> &out,
+// (kMinK <= k <= min(kMaxK, n)). `pin0` is set for 8-byte amplitudes: tile
+// position 0 stays on register bit 3 in every layout (the kernel packs the two
+// amplitudes that differ in qubit 0 into one f32x2 register and moves them as
+// one 8-byte unit), and the load/store layout puts lanes on positions 1..5
+// (one 16-byte access = the two amplitudes of one packed pair). Without pin0
+// (16-byte amplitudes) lanes of the load/store layout sit on positions 0..4.
+// Returns false with `err` set on failure.
+// `fuse` = false keeps one op per gate.
+bool make_plan(int n, int k, bool pin0, bool fuse, const std::vector<PGate> &gates, std::vector<Pass> &out,
                PlanStats &stats, std::string &err);
 
 // Classifies a 2x2 matrix: G_DIAG if off-diagonal entries are 0, G_X if it is

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libqv.so")
 QV_C64, QV_C128 = 0, 1
 QV_OK, QV_ERR_ARG, QV_ERR_OOM, QV_ERR_CUDA, QV_ERR_TIMEOUT, QV_ERR_UNSUPPORTED = range(6)
 QV_MODE_AUTO, QV_MODE_PLAIN, QV_MODE_FUSED = 0, 1, 2
+QV_PLAN_NO_FUSION = 1
 STATUS_NAMES = {0: "QV_OK", 1: "QV_ERR_ARG", 2: "QV_ERR_OOM", 3: "QV_ERR_CUDA",
                 4: "QV_ERR_TIMEOUT", 5: "QV_ERR_UNSUPPORTED"}
 KIND = {"h": 0, "x": 1, "y": 2, "z": 3, "s": 4, "sdg": 5, "t": 6, "tdg": 7,
@@ -41,7 +42,8 @@ class qv_gate(ctypes.Structure):
 
 
 class qv_plan_opts(ctypes.Structure):
-    _fields_ = [("mode", ctypes.c_int32), ("tile_bits", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+    _fields_ = [("mode", ctypes.c_int32), ("tile_bits", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class qv_kernel_stat(ctypes.Structure):
@@ -154,10 +156,11 @@ def terms_to_c(terms: Sequence[Tuple[float, int, int]]) -> ctypes.Array:
     return arr
 
 
-def plan_opts(mode: int = QV_MODE_AUTO, tile_bits: int = 0) -> qv_plan_opts:
+def plan_opts(mode: int = QV_MODE_AUTO, tile_bits: int = 0, flags: int = 0) -> qv_plan_opts:
     o = qv_plan_opts()
     o.mode = mode
     o.tile_bits = tile_bits
+    o.flags = flags
     return o
 
 
@@ -215,25 +218,25 @@ def qv_apply_controlled(h: int, ctrl: int, target: int, U):
     _check(lib.qv_apply_controlled(h, ctrl, target, c128_array(U)))
 
 
-def qv_apply_circuit(h: int, gates, mode: int = QV_MODE_AUTO, tile_bits: int = 0):
+def qv_apply_circuit(h: int, gates, mode: int = QV_MODE_AUTO, tile_bits: int = 0, flags: int = 0):
     """``gates``: a sequence of workloads.Gate or a prebuilt qv_gate array
     (``gates_to_c``) with its length as ``(array, count)``."""
     if isinstance(gates, tuple) and len(gates) == 2 and isinstance(gates[1], int):
         arr, ng = gates
     else:
         arr, ng = gates_to_c(gates), len(gates)
-    opts = plan_opts(mode, tile_bits)
+    opts = plan_opts(mode, tile_bits, flags)
     _check(lib.qv_apply_circuit(h, arr, ng, ctypes.byref(opts)))
 
 
-def qv_plan_info(n: int, dtype: int, gates, tile_bits: int = 0) -> dict:
+def qv_plan_info(n: int, dtype: int, gates, tile_bits: int = 0, flags: int = 0) -> dict:
     """Fused-mode plan of ``gates`` (host only): passes, stages, transposes, ops."""
     if isinstance(gates, tuple) and len(gates) == 2 and isinstance(gates[1], int):
         arr, ng = gates
     else:
         arr, ng = gates_to_c(gates), len(gates)
     out = (ctypes.c_int32 * 4)()
-    opts = plan_opts(QV_MODE_FUSED, tile_bits)
+    opts = plan_opts(QV_MODE_FUSED, tile_bits, flags)
     _check(lib.qv_plan_info(n, dtype, arr, ng, ctypes.byref(opts), out))
     return {"passes": out[0], "stages": out[1], "transposes": out[2], "ops": out[3]}
 
