@@ -83,6 +83,9 @@ typedef enum {
 
 /* qv_plan_opts.flags */
 #define QV_PLAN_NO_FUSION 1  /* fused mode: one on-chip operation per gate (no 2x2 products) */
+#define QV_PLAN_INTERPRET 2  /* fused mode: run the planner's program with the precompiled
+                                interpreting kernel instead of compiling each pass (NVRTC);
+                                also used when NVRTC cannot be loaded */
 
 typedef struct {
     int32_t mode;        /* qv_mode */

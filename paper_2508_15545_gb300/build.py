@@ -74,7 +74,7 @@ def build(force: bool = False, debug: bool = False, verbose: bool = False) -> st
                     print(futs[f], msg, file=sys.stderr)
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".%d.tmp" % os.getpid()
-        cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcuda"]
+        cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))

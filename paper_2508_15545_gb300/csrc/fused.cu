@@ -18,9 +18,11 @@
 #include <mutex>
 #include <vector>
 
+#include "coef.h"
 #include "planner.h"
 #include "qv_device.cuh"
 #include "qv_internal.h"
+#include "qv_jit.h"
 #include "qv_plan.h"
 
 namespace qv {
@@ -616,58 +618,8 @@ __global__ void __launch_bounds__(1 << (K - kRegBits), QV_FUSED_MINB(R, K)) fuse
 }
 
 // ---------------------------------------------------------------- host side
-uint64_t pack2(float lo, float hi)
-{
-    uint32_t a, b;
-    memcpy(&a, &lo, 4);
-    memcpy(&b, &hi, 4);
-    return uint64_t(a) | (uint64_t(b) << 32);
-}
-
-// (re, im, -im) of z0 in lane 0 and z1 in lane 1
-void lanes(uint64_t *dst, std::complex<double> z0, std::complex<double> z1)
-{
-    dst[0] = pack2(float(z0.real()), float(z1.real()));
-    dst[1] = pack2(float(z0.imag()), float(z1.imag()));
-    dst[2] = pack2(float(-z0.imag()), float(-z1.imag()));
-}
-
-void fill_coeffs(DOp<float> &d, const plan::Op &op)
-{
-    if (op.type == plan::OP_DIAG) {
-        if (op.sreg == 3) {  // select on the lane bit: lane 0 = select 0, lane 1 = select 1
-            lanes(d.c[0], op.M[0][0], op.M[1][0]);
-            lanes(d.c[0] + 3, op.M[0][3], op.M[1][3]);
-            return;
-        }
-        for (int s = 0; s < 2; ++s) {
-            if (op.treg == 3) {  // target on the lane bit: lane 0 takes d0, lane 1 d1
-                lanes(d.c[s], op.M[s][0], op.M[s][3]);
-            } else {
-                lanes(d.c[s], op.M[s][0], op.M[s][0]);
-                lanes(d.c[s] + 3, op.M[s][3], op.M[s][3]);
-            }
-        }
-        return;
-    }
-    for (int e = 0; e < 4; ++e) {
-        if (op.sreg == 3) {
-            lanes(d.c[0] + 3 * e, op.M[0][e], op.M[1][e]);
-        } else {
-            lanes(d.c[0] + 3 * e, op.M[0][e], op.M[0][e]);
-            lanes(d.c[1] + 3 * e, op.M[1][e], op.M[1][e]);
-        }
-    }
-}
-
-void fill_coeffs(DOp<double> &d, const plan::Op &op)
-{
-    for (int s = 0; s < 2; ++s)
-        for (int e = 0; e < 4; ++e) {
-            d.m[s][2 * e] = op.M[s][e].real();
-            d.m[s][2 * e + 1] = op.M[s][e].imag();
-        }
-}
+void fill_coeffs(DOp<float> &d, const plan::Op &op) { op_coeffs_c64(op, &d.c[0][0]); }
+void fill_coeffs(DOp<double> &d, const plan::Op &op) { op_coeffs_c128(op, &d.m[0][0]); }
 
 template <typename R> void serialize(const plan::Pass &p, std::vector<unsigned char> &buf)
 {
@@ -842,6 +794,7 @@ qv_status apply_fused(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_op
     const bool fuse = !(opts && (opts->flags & QV_PLAN_NO_FUSION));
     if (!plan::make_plan(s->n, K, s->dt == QV_C64, fuse, pg, passes, st, err))
         return fail(QV_ERR_UNSUPPORTED, "planner: %s", err.c_str());
+    if (!(opts && (opts->flags & QV_PLAN_INTERPRET)) && jit_available(nullptr)) return jit_run_plan(s, passes);
     return s->dt == QV_C64 ? run_plan<float>(s, passes, K) : run_plan<double>(s, passes, K);
 }
 

@@ -1,0 +1,613 @@
+// Compiled fused passes. The planner's program for one pass (tile qubits,
+// register layouts, the op sequence) is turned into CUDA C++ with every
+// layout, address offset, target and select bit baked in as constants, then
+// compiled with NVRTC for sm_103a and launched through the driver API. The
+// gate coefficients stay runtime data (a by-value kernel parameter, read
+// from the constant bank), so circuits that differ only in their angles --
+// the same circuit run again, or a variational ansatz with new parameters --
+// reuse the compiled kernel. Compared with the interpreted kernel in
+// fused.cu this removes the per-op dispatch, the register moves at the
+// dispatch merge points, and the runtime index arithmetic.
+#include <cuda.h>
+#include <dlfcn.h>
+#include <nvrtc.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "coef.h"
+#include "planner.h"
+#include "qv_internal.h"
+#include "qv_jit.h"
+
+namespace qv {
+namespace {
+
+using plan::kChunkBits;
+using plan::kRegBits;
+
+// ---------------------------------------------------------------- NVRTC + driver, loaded on demand
+// Both are opened with dlopen so that libqv.so itself loads on machines
+// without a GPU driver (the host-only entry points still work there).
+struct JitApi {
+    bool ok = false;
+    std::string why;
+    nvrtcResult (*create)(nvrtcProgram *, const char *, const char *, int, const char *const *, const char *const *);
+    nvrtcResult (*compile)(nvrtcProgram, int, const char *const *);
+    nvrtcResult (*log_size)(nvrtcProgram, size_t *);
+    nvrtcResult (*log)(nvrtcProgram, char *);
+    nvrtcResult (*cubin_size)(nvrtcProgram, size_t *);
+    nvrtcResult (*cubin)(nvrtcProgram, char *);
+    nvrtcResult (*destroy)(nvrtcProgram *);
+    CUresult (*module_load)(CUmodule *, const void *);
+    CUresult (*get_function)(CUfunction *, CUmodule, const char *);
+    CUresult (*set_attr)(CUfunction, CUfunction_attribute, int);
+    CUresult (*occupancy)(int *, CUfunction, int, size_t);
+    CUresult (*launch)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, CUstream,
+                       void **, void **);
+    CUresult (*err_string)(CUresult, const char **);
+};
+
+const JitApi &api()
+{
+    static JitApi n;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *h = dlopen("libnvrtc.so.13", RTLD_NOW | RTLD_LOCAL);
+        if (!h) h = dlopen("libnvrtc.so", RTLD_NOW | RTLD_LOCAL);
+        void *d = dlopen("libcuda.so.1", RTLD_NOW | RTLD_LOCAL);
+        if (!h || !d) {
+            n.why = !h ? "libnvrtc.so not found" : "libcuda.so.1 not found";
+            return;
+        }
+        bool all = true;
+        auto sym = [&](void *lib, auto &f, const char *name) {
+            f = reinterpret_cast<std::remove_reference_t<decltype(f)>>(dlsym(lib, name));
+            all &= f != nullptr;
+        };
+        sym(h, n.create, "nvrtcCreateProgram");
+        sym(h, n.compile, "nvrtcCompileProgram");
+        sym(h, n.log_size, "nvrtcGetProgramLogSize");
+        sym(h, n.log, "nvrtcGetProgramLog");
+        sym(h, n.cubin_size, "nvrtcGetCUBINSize");
+        sym(h, n.cubin, "nvrtcGetCUBIN");
+        sym(h, n.destroy, "nvrtcDestroyProgram");
+        sym(d, n.module_load, "cuModuleLoadData");
+        sym(d, n.get_function, "cuModuleGetFunction");
+        sym(d, n.set_attr, "cuFuncSetAttribute");
+        sym(d, n.occupancy, "cuOccupancyMaxActiveBlocksPerMultiprocessor");
+        sym(d, n.launch, "cuLaunchKernel");
+        sym(d, n.err_string, "cuGetErrorString");
+        n.ok = all;
+        if (!all) n.why = "libnvrtc.so or libcuda.so.1 lacks a needed symbol";
+    });
+    return n;
+}
+
+// ---------------------------------------------------------------- device prelude
+const char *kPrelude = R"PRELUDE(
+typedef unsigned long long u64;
+typedef unsigned int u32;
+#define QI __device__ __forceinline__
+QI u64 pk(float lo, float hi) { u64 r; asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi)); return r; }
+QI void upk(u64 v, float &lo, float &hi) { asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v)); }
+QI u64 f2fma(u64 a, u64 b, u64 c) { u64 d; asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c)); return d; }
+QI u64 f2mul(u64 a, u64 b) { u64 d; asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b)); return d; }
+
+// complex64: (a, b) <- U (a, b) on two packed pairs; c = (re, im, -im) pairs of U00 U01 U10 U11
+QI void ap2(const u64 (&c)[12], u64 &ar, u64 &ai, u64 &br, u64 &bi) {
+    const u64 xr = ar, xi = ai, yr = br, yi = bi;
+    ar = f2fma(c[0], xr, f2fma(c[2], xi, f2fma(c[3], yr, f2mul(c[5], yi))));
+    ai = f2fma(c[0], xi, f2fma(c[1], xr, f2fma(c[3], yi, f2mul(c[4], yr))));
+    br = f2fma(c[6], xr, f2fma(c[8], xi, f2fma(c[9], yr, f2mul(c[11], yi))));
+    bi = f2fma(c[6], xi, f2fma(c[7], xr, f2fma(c[9], yi, f2mul(c[10], yr))));
+}
+QI void cm2(u64 dr, u64 di, u64 dn, u64 &ar, u64 &ai) {
+    const u64 xr = ar, xi = ai;
+    ar = f2fma(dr, xr, f2mul(dn, xi));
+    ai = f2fma(dr, xi, f2mul(di, xr));
+}
+// scalar pair with the lane-0 values of c
+QI void ap1(const u64 (&c)[12], float &ar, float &ai, float &br, float &bi) {
+    float u[8], t;
+    for (int e = 0; e < 4; ++e) { upk(c[3 * e], u[2 * e], t); upk(c[3 * e + 1], u[2 * e + 1], t); }
+    const float xr = ar, xi = ai, yr = br, yi = bi;
+    ar = u[0] * xr - u[1] * xi + u[2] * yr - u[3] * yi;
+    ai = u[0] * xi + u[1] * xr + u[2] * yi + u[3] * yr;
+    br = u[4] * xr - u[5] * xi + u[6] * yr - u[7] * yi;
+    bi = u[4] * xi + u[5] * xr + u[6] * yi + u[7] * yr;
+}
+template <int J> QI void g_all(u64 (&r)[8], u64 (&i)[8], const u64 (&c)[12]) {
+#pragma unroll
+    for (int v = 0; v < 8; ++v) if (!((v >> J) & 1)) ap2(c, r[v], i[v], r[v | (1 << J)], i[v | (1 << J)]);
+}
+template <int J, int C, int S> QI void g_sel(u64 (&r)[8], u64 (&i)[8], const u64 (&c)[12]) {
+#pragma unroll
+    for (int v = 0; v < 8; ++v)
+        if (!((v >> J) & 1) && ((v >> C) & 1) == S) ap2(c, r[v], i[v], r[v | (1 << J)], i[v | (1 << J)]);
+}
+template <int C, int S> QI void g_lane(u64 (&r)[8], u64 (&i)[8], const u64 (&c)[12]) {
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        if (C >= 0 && ((v >> C) & 1) != S) continue;
+        float a0, a1, b0, b1;
+        upk(r[v], a0, a1); upk(i[v], b0, b1);
+        ap1(c, a0, b0, a1, b1);
+        r[v] = pk(a0, a1); i[v] = pk(b0, b1);
+    }
+}
+template <int J, int C> QI void x_op(u64 (&r)[8], u64 (&i)[8]) {
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        if (J < 3) {
+            if ((v >> J) & 1) continue;
+            const int w = v | (1 << (J & 3));
+            if (C == 3) {
+                float a0, a1, b0, b1, c0, c1, d0, d1;
+                upk(r[v], a0, a1); upk(i[v], b0, b1); upk(r[w], c0, c1); upk(i[w], d0, d1);
+                r[v] = pk(a0, c1); i[v] = pk(b0, d1); r[w] = pk(c0, a1); i[w] = pk(d0, b1);
+            } else {
+                if (C >= 0 && !((v >> (C & 3)) & 1)) continue;
+                const u64 tr = r[v], ti = i[v];
+                r[v] = r[w]; i[v] = i[w]; r[w] = tr; i[w] = ti;
+            }
+        } else {
+            if (C >= 0 && !((v >> (C & 3)) & 1)) continue;
+            float a0, a1, b0, b1;
+            upk(r[v], a0, a1); upk(i[v], b0, b1);
+            r[v] = pk(a1, a0); i[v] = pk(b1, b0);
+        }
+    }
+}
+// diagonal: c[0..2] = d0, c[3..5] = d1 (lane-resolved by the host where lanes differ);
+// J = 0..2 register target, 3 = lane target, 4 = uniform target given by t1
+template <int J, int C, int S> QI void d_op(u64 (&r)[8], u64 (&i)[8], const u64 (&c)[12], bool t1) {
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        if (!(C < 0 || C == 3 || ((v >> (C & 3)) & 1) == S)) continue;
+        bool one;
+        if (J == 4) one = t1; else if (J == 3) one = false; else one = ((v >> (J & 3)) & 1) != 0;
+        if (one) cm2(c[3], c[4], c[5], r[v], i[v]); else cm2(c[0], c[1], c[2], r[v], i[v]);
+    }
+}
+
+// complex128, scalar slots m = 0..15; m8 = re, im of U00 U01 U10 U11
+QI void ap1d(const double (&m)[8], double &ar, double &ai, double &br, double &bi) {
+    const double xr = ar, xi = ai, yr = br, yi = bi;
+    ar = m[0] * xr - m[1] * xi + m[2] * yr - m[3] * yi;
+    ai = m[0] * xi + m[1] * xr + m[2] * yi + m[3] * yr;
+    br = m[4] * xr - m[5] * xi + m[6] * yr - m[7] * yi;
+    bi = m[4] * xi + m[5] * xr + m[6] * yi + m[7] * yr;
+}
+template <int J, int C, int S> QI void g_d(double (&r)[16], double (&i)[16], const double (&m)[8]) {
+#pragma unroll
+    for (int s = 0; s < 16; ++s)
+        if (!((s >> J) & 1) && (C < 0 || ((s >> (C & 3)) & 1) == S)) ap1d(m, r[s], i[s], r[s | (1 << J)], i[s | (1 << J)]);
+}
+template <int J, int C> QI void x_d(double (&r)[16], double (&i)[16]) {
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+        if (((s >> J) & 1) || (C >= 0 && !((s >> (C & 3)) & 1))) continue;
+        const int w = s | (1 << J);
+        const double tr = r[s], ti = i[s];
+        r[s] = r[w]; i[s] = i[w]; r[w] = tr; i[w] = ti;
+    }
+}
+template <int J, int C, int S> QI void d_d(double (&r)[16], double (&i)[16], const double (&m)[8], bool t1) {
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+        if (!(C < 0 || ((s >> (C & 3)) & 1) == S)) continue;
+        const bool one = J == 4 ? t1 : (((s >> (J & 3)) & 1) != 0);
+        const double dr = one ? m[6] : m[0], di = one ? m[7] : m[1];
+        const double xr = r[s];
+        r[s] = dr * xr - di * i[s];
+        i[s] = dr * i[s] + di * xr;
+    }
+}
+)PRELUDE";
+
+// ---------------------------------------------------------------- source generation
+uint32_t swz8(uint32_t w) { return w ^ (((w >> 4) ^ (w >> 8)) & 15u); }
+uint32_t swz16(uint32_t w) { return w ^ (((w >> 3) ^ (w >> 6) ^ (w >> 9)) & 7u); }
+
+struct PassGeom {
+    int k, nq, nh;
+    const plan::Pass *p;
+    uint64_t phys(uint32_t l) const
+    {
+        uint64_t g = l & ((1u << kChunkBits) - 1);
+        for (int j = 0; j < nh; ++j)
+            if ((l >> (kChunkBits + j)) & 1) g |= uint64_t(1) << p->s_high[j];
+        return g;
+    }
+};
+
+std::string hex64(uint64_t v)
+{
+    char b[32];
+    snprintf(b, sizeof b, "0x%llxull", (unsigned long long)v);
+    return b;
+}
+std::string hex32(uint32_t v)
+{
+    char b[32];
+    snprintf(b, sizeof b, "0x%xu", v);
+    return b;
+}
+
+// XOR over thread bits b of (bit b of tid ? mask[b] : 0)
+std::string thread_expr(const std::vector<uint64_t> &mask, bool wide)
+{
+    std::string e = wide ? "0ull" : "0u";
+    for (size_t b = 0; b < mask.size(); ++b) {
+        if (!mask[b]) continue;
+        if (wide)
+            e += " ^ ((0ull - (u64)((tid >> " + std::to_string(b) + ") & 1u)) & " + hex64(mask[b]) + ")";
+        else
+            e += " ^ ((0u - ((tid >> " + std::to_string(b) + ") & 1u)) & " + hex32(uint32_t(mask[b])) + ")";
+    }
+    return "(" + e + ")";
+}
+
+std::string coef_load(int base, const std::string &sel, int n, bool dbl)
+{
+    std::ostringstream o;
+    o << (dbl ? "double m[8];" : "u64 c[12];");
+    for (int e = 0; e < n; ++e)
+        o << (dbl ? " m[" : " c[") << e << "] = cf.c[" << base << " + " << (dbl ? 8 : 12) << " * (" << sel << ") + " << e
+          << "];";
+    return o.str();
+}
+
+void emit_op_c64(std::ostream &o, const plan::Op &op, int k)
+{
+    const int O = 24 * k;
+    const bool us = op.sthr || op.sext;
+    const std::string sel =
+        us ? "(((tid & " + hex32(op.sthr) + ") != 0u) | ((base & " + hex64(op.sext) + ") != 0ull))" : "0";
+    const int J = op.treg, C = op.sreg;
+    if (op.type == plan::OP_GEN) {
+        if (C < 0) {
+            o << "    { const int s = " << sel << "; if (s || " << (op.m0id ? 0 : 1) << ") { " << coef_load(O, "s", 12, false);
+            o << (J < 3 ? " g_all<" + std::to_string(J) + ">(r, i, c);" : " g_lane<-1, 0>(r, i, c);") << " } }\n";
+        } else if (C == 3) {
+            o << "    { " << coef_load(O, "0", 12, false) << " g_all<" << J << ">(r, i, c); }\n";
+        } else {
+            for (int s = 0; s < 2; ++s) {
+                if (s == 0 && op.m0id) continue;
+                o << "    { " << coef_load(O, std::to_string(s), 12, false);
+                if (J < 3) o << " g_sel<" << J << ", " << C << ", " << s << ">(r, i, c); }\n";
+                else o << " g_lane<" << C << ", " << s << ">(r, i, c); }\n";
+            }
+        }
+    } else if (op.type == plan::OP_X) {
+        if (C < 0 && us && op.m0id) o << "    if (" << sel << ") x_op<" << J << ", -1>(r, i);\n";
+        else o << "    x_op<" << J << ", " << C << ">(r, i);\n";
+    } else {
+        const int Jd = J >= 0 ? J : 4;
+        const std::string t1 = Jd == 4 ? "(((tid & " + hex32(op.tthr) + ") != 0u) | ((base & " + hex64(op.text) +
+                                             ") != 0ull))"
+                                       : "false";
+        if (C < 0) {
+            o << "    { const int s = " << sel << "; if (s || " << (op.m0id ? 0 : 1) << ") { " << coef_load(O, "s", 6, false)
+              << " d_op<" << Jd << ", -1, 0>(r, i, c, " << t1 << "); } }\n";
+        } else if (C == 3) {
+            o << "    { " << coef_load(O, "0", 6, false) << " d_op<" << Jd << ", 3, 0>(r, i, c, " << t1 << "); }\n";
+        } else {
+            for (int s = 0; s < 2; ++s) {
+                if (s == 0 && op.m0id) continue;
+                o << "    { " << coef_load(O, std::to_string(s), 6, false) << " d_op<" << Jd << ", " << C << ", " << s
+                  << ">(r, i, c, " << t1 << "); }\n";
+            }
+        }
+    }
+}
+
+void emit_op_c128(std::ostream &o, const plan::Op &op, int k)
+{
+    const int O = 16 * k;
+    const bool us = op.sthr || op.sext;
+    const std::string sel =
+        us ? "(((tid & " + hex32(op.sthr) + ") != 0u) | ((base & " + hex64(op.sext) + ") != 0ull))" : "0";
+    const int J = op.treg, C = op.sreg;
+    if (op.type == plan::OP_X) {
+        if (C < 0 && us && op.m0id) o << "    if (" << sel << ") x_d<" << J << ", -1>(r, i);\n";
+        else o << "    x_d<" << J << ", " << C << ">(r, i);\n";
+        return;
+    }
+    const bool diag = op.type == plan::OP_DIAG;
+    const int Jd = diag && J < 0 ? 4 : J;
+    const std::string t1 = Jd == 4 ? "(((tid & " + hex32(op.tthr) + ") != 0u) | ((base & " + hex64(op.text) +
+                                         ") != 0ull))"
+                                   : "false";
+    auto call = [&](int c, int s) {
+        std::ostringstream x;
+        if (diag) x << " d_d<" << Jd << ", " << c << ", " << s << ">(r, i, m, " << t1 << ");";
+        else x << " g_d<" << J << ", " << c << ", " << s << ">(r, i, m);";
+        return x.str();
+    };
+    if (C < 0) {
+        o << "    { const int s = " << sel << "; if (s || " << (op.m0id ? 0 : 1) << ") { " << coef_load(O, "s", 8, true)
+          << call(-1, 0) << " } }\n";
+    } else {
+        for (int s = 0; s < 2; ++s) {
+            if (s == 0 && op.m0id) continue;
+            o << "    { " << coef_load(O, std::to_string(s), 8, true) << call(C, s) << " }\n";
+        }
+    }
+}
+
+int min_blocks(bool c64, int k) { return k == 12 ? (c64 ? 3 : 1) : (c64 ? 4 : 2); }
+
+std::string gen_source(const plan::Pass &p, bool c64)
+{
+    PassGeom G{p.k, p.k - kRegBits, p.k - kChunkBits, &p};
+    const int T = 1 << G.nq;
+    const int nops = int(p.ops.size());
+    const int ncoef = std::max(1, nops * (c64 ? 24 : 16));
+    const int nreg = c64 ? 3 : 4;  // register bits addressed per vector/slot (c64: bit 3 is the lane)
+    const int nvec = 1 << nreg;
+    std::ostringstream o;
+    o << kPrelude;
+    o << "struct QvCoef { " << (c64 ? "u64" : "double") << " c[" << ncoef << "]; };\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(" << T << ", " << min_blocks(c64, p.k) << ") qv_pass("
+      << (c64 ? "float" : "double") << " *__restrict__ amp, u64 ntiles, const QvCoef cf)\n{\n";
+    o << "    extern __shared__ __align__(16) u64 sm[];\n";
+    o << "    const u32 tid = threadIdx.x;\n";
+    // loop-invariant thread offsets
+    auto phys_mask = [&](const int8_t *Q) {
+        std::vector<uint64_t> m(G.nq);
+        for (int b = 0; b < G.nq; ++b) m[b] = G.phys(1u << Q[b]);
+        return m;
+    };
+    auto word_mask = [&](const int8_t *Q) {
+        std::vector<uint64_t> m(G.nq);
+        for (int b = 0; b < G.nq; ++b) m[b] = c64 ? swz8((1u << Q[b]) >> 1) : swz16(1u << Q[b]);
+        return m;
+    };
+    const plan::Stage &s0 = p.stages.front(), &sl = p.stages.back();
+    o << "    const u64 gL = " << thread_expr(phys_mask(s0.in.Q), true) << ";\n";
+    o << "    const u64 gS = " << thread_expr(phys_mask(sl.out.Q), true) << ";\n";
+    for (size_t s = 1; s < p.stages.size(); ++s) {
+        o << "    const u32 wW" << s << " = " << thread_expr(word_mask(p.stages[s - 1].out.Q), false) << ";\n";
+        o << "    const u32 wR" << s << " = " << thread_expr(word_mask(p.stages[s].in.Q), false) << ";\n";
+    }
+    o << "    for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {\n";
+    o << "    const u64 base = 0ull";
+    for (int s = 0; s < p.nseg; ++s)
+        o << " | (((t >> " << p.seg_src[s] << ") & " << hex64((uint64_t(1) << p.seg_w[s]) - 1) << ") << "
+          << p.seg_dst[s] << ")";
+    o << ";\n";
+    auto reg_offset = [&](const int8_t *P, int v) {
+        uint32_t l = 0;
+        for (int j = 0; j < nreg; ++j)
+            if ((v >> j) & 1) l |= 1u << P[j];
+        return l;
+    };
+    if (c64) {
+        o << "    u64 r[8], i[8];\n";
+        o << "    { const float *a = amp + 2 * (base + gL);\n";
+        for (int v = 0; v < 8; ++v)
+            o << "      const float4 f" << v << " = *reinterpret_cast<const float4 *>(a + 2 * "
+              << hex64(G.phys(reg_offset(s0.in.P, v))) << ");\n";
+        for (int v = 0; v < 8; ++v)
+            o << "      r[" << v << "] = pk(f" << v << ".x, f" << v << ".z); i[" << v << "] = pk(f" << v << ".y, f" << v
+              << ".w);\n";
+        o << "    }\n";
+    } else {
+        o << "    double r[16], i[16];\n";
+        o << "    { const double2 *a = reinterpret_cast<const double2 *>(amp) + (base + gL);\n";
+        for (int m = 0; m < 16; ++m)
+            o << "      const double2 f" << m << " = a[" << hex64(G.phys(reg_offset(s0.in.P, m))) << "];\n";
+        for (int m = 0; m < 16; ++m) o << "      r[" << m << "] = f" << m << ".x; i[" << m << "] = f" << m << ".y;\n";
+        o << "    }\n";
+    }
+    for (size_t s = 0; s < p.stages.size(); ++s) {
+        const plan::Stage &st = p.stages[s];
+        if (s > 0) {
+            const plan::Stage &pr = p.stages[s - 1];
+            if (c64) {
+                o << "    { u64 *pre = sm, *pim = sm + " << (1 << (p.k - 1)) << ";\n";
+                for (int v = 0; v < nvec; ++v) {
+                    const uint32_t w = swz8(reg_offset(pr.out.P, v) >> 1);
+                    o << "      pre[wW" << s << " ^ " << hex32(w) << "] = r[" << v << "]; pim[wW" << s << " ^ " << hex32(w)
+                      << "] = i[" << v << "];\n";
+                }
+                o << "      __syncthreads();\n";
+                for (int v = 0; v < nvec; ++v) {
+                    const uint32_t w = swz8(reg_offset(st.in.P, v) >> 1);
+                    o << "      r[" << v << "] = pre[wR" << s << " ^ " << hex32(w) << "]; i[" << v << "] = pim[wR" << s
+                      << " ^ " << hex32(w) << "];\n";
+                }
+                o << "      __syncthreads(); }\n";
+            } else {
+                o << "    { double2 *tl = reinterpret_cast<double2 *>(sm);\n";
+                for (int v = 0; v < nvec; ++v) {
+                    const uint32_t w = swz16(reg_offset(pr.out.P, v));
+                    o << "      tl[wW" << s << " ^ " << hex32(w) << "] = make_double2(r[" << v << "], i[" << v << "]);\n";
+                }
+                o << "      __syncthreads();\n";
+                for (int v = 0; v < nvec; ++v) {
+                    const uint32_t w = swz16(reg_offset(st.in.P, v));
+                    o << "      { const double2 q = tl[wR" << s << " ^ " << hex32(w) << "]; r[" << v << "] = q.x; i[" << v
+                      << "] = q.y; }\n";
+                }
+                o << "      __syncthreads(); }\n";
+            }
+        }
+        for (int k = st.op_begin; k < st.op_end; ++k) {
+            if (c64) emit_op_c64(o, p.ops[k], k);
+            else emit_op_c128(o, p.ops[k], k);
+        }
+    }
+    if (c64) {
+        o << "    { float *a = amp + 2 * (base + gS); float x0, x1, y0, y1;\n";
+        for (int v = 0; v < 8; ++v)
+            o << "      upk(r[" << v << "], x0, x1); upk(i[" << v << "], y0, y1); *reinterpret_cast<float4 *>(a + 2 * "
+              << hex64(G.phys(reg_offset(sl.out.P, v))) << ") = make_float4(x0, y0, x1, y1);\n";
+        o << "    }\n";
+    } else {
+        o << "    { double2 *a = reinterpret_cast<double2 *>(amp) + (base + gS);\n";
+        for (int m = 0; m < 16; ++m)
+            o << "      a[" << hex64(G.phys(reg_offset(sl.out.P, m))) << "] = make_double2(r[" << m << "], i[" << m
+              << "]);\n";
+        o << "    }\n";
+    }
+    o << "    }\n}\n";
+    return o.str();
+}
+
+// ---------------------------------------------------------------- compile + cache
+struct Compiled {
+    CUmodule mod = nullptr;
+    CUfunction fn = nullptr;
+    int per_sm = 0;
+    size_t smem = 0;
+};
+
+std::mutex g_cache_mu;
+std::map<std::pair<int, std::string>, std::shared_ptr<Compiled>> g_cache;
+
+bool compile_one(const std::string &src, std::vector<char> &cubin, std::string &err)
+{
+    const JitApi &N = api();
+    nvrtcProgram prog;
+    if (N.create(&prog, src.c_str(), "qv_pass.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+        err = "nvrtcCreateProgram failed";
+        return false;
+    }
+    const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "--fmad=true"};
+    const nvrtcResult rc = N.compile(prog, 3, opts);
+    if (rc != NVRTC_SUCCESS) {
+        size_t ls = 0;
+        N.log_size(prog, &ls);
+        std::string log(ls, '\0');
+        if (ls) N.log(prog, &log[0]);
+        err = "nvrtc: " + log.substr(0, 400);
+        N.destroy(&prog);
+        return false;
+    }
+    size_t cs = 0;
+    N.cubin_size(prog, &cs);
+    cubin.resize(cs);
+    N.cubin(prog, cubin.data());
+    N.destroy(&prog);
+    return true;
+}
+
+qv_status cu_fail(CUresult r, const char *what)
+{
+    const char *s = nullptr;
+    if (api().err_string) api().err_string(r, &s);
+    return fail(QV_ERR_CUDA, "%s: %s", what, s ? s : "?");
+}
+
+}  // namespace
+
+bool jit_available(std::string *why)
+{
+    const JitApi &N = api();
+    if (!N.ok && why) *why = N.why;
+    return N.ok;
+}
+
+qv_status jit_run_plan(qv_state *s, const std::vector<plan::Pass> &passes)
+{
+    const bool c64 = s->dt == QV_C64;
+    std::string why;
+    if (!jit_available(&why)) return fail(QV_ERR_UNSUPPORTED, "compiled fused passes unavailable: %s", why.c_str());
+    // make sure this thread has the device's primary context current for the driver API
+    QV_CUDA(cudaSetDevice(s->device));
+    QV_CUDA(cudaFree(nullptr));
+
+    std::vector<std::string> srcs(passes.size());
+    std::vector<std::shared_ptr<Compiled>> fns(passes.size());
+    std::vector<size_t> todo;
+    {
+        std::lock_guard<std::mutex> lock(g_cache_mu);
+        for (size_t i = 0; i < passes.size(); ++i) {
+            srcs[i] = gen_source(passes[i], c64);
+            auto it = g_cache.find({s->device, srcs[i]});
+            if (it != g_cache.end()) fns[i] = it->second;
+            else if (std::find_if(todo.begin(), todo.end(), [&](size_t j) { return srcs[j] == srcs[i]; }) == todo.end())
+                todo.push_back(i);
+        }
+    }
+    if (!todo.empty()) {
+        std::vector<std::vector<char>> cubins(todo.size());
+        std::vector<std::string> errs(todo.size());
+        std::vector<char> okv(todo.size(), 0);
+        const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        size_t next = 0;
+        std::mutex mu;
+        auto worker = [&] {
+            for (;;) {
+                size_t j;
+                {
+                    std::lock_guard<std::mutex> l(mu);
+                    if (next >= todo.size()) return;
+                    j = next++;
+                }
+                okv[j] = compile_one(srcs[todo[j]], cubins[j], errs[j]);
+            }
+        };
+        std::vector<std::thread> th;
+        for (unsigned w = 0; w < std::min<size_t>(hw, todo.size()); ++w) th.emplace_back(worker);
+        for (auto &t : th) t.join();
+        std::lock_guard<std::mutex> lock(g_cache_mu);
+        for (size_t j = 0; j < todo.size(); ++j) {
+            if (!okv[j]) return fail(QV_ERR_CUDA, "compiling a fused pass failed: %s", errs[j].c_str());
+            auto c = std::make_shared<Compiled>();
+            const JitApi &A = api();
+            CUresult r = A.module_load(&c->mod, cubins[j].data());
+            if (r != CUDA_SUCCESS) return cu_fail(r, "cuModuleLoadData");
+            r = A.get_function(&c->fn, c->mod, "qv_pass");
+            if (r != CUDA_SUCCESS) return cu_fail(r, "cuModuleGetFunction");
+            const int k = passes[todo[j]].k;
+            c->smem = (c64 ? 8 : 16) * (size_t(1) << k);
+            if (c->smem > 48 * 1024) {
+                r = A.set_attr(c->fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, int(c->smem));
+                if (r != CUDA_SUCCESS) return cu_fail(r, "cuFuncSetAttribute");
+            }
+            r = A.occupancy(&c->per_sm, c->fn, 1 << (k - kRegBits), c->smem);
+            if (r != CUDA_SUCCESS) return cu_fail(r, "cuOccupancyMaxActiveBlocksPerMultiprocessor");
+            if (c->per_sm < 1) return fail(QV_ERR_UNSUPPORTED, "compiled pass does not fit on an SM");
+            g_cache[{s->device, srcs[todo[j]]}] = c;
+        }
+        for (size_t i = 0; i < passes.size(); ++i)
+            if (!fns[i]) fns[i] = g_cache[{s->device, srcs[i]}];
+    }
+    // launch every pass with its coefficients as a by-value parameter
+    std::vector<uint64_t> coef;
+    for (size_t i = 0; i < passes.size(); ++i) {
+        const plan::Pass &p = passes[i];
+        const size_t per = c64 ? 24 : 16;
+        coef.assign(std::max<size_t>(1, p.ops.size() * per), 0);
+        for (size_t k = 0; k < p.ops.size(); ++k) {
+            if (c64) op_coeffs_c64(p.ops[k], coef.data() + k * per);
+            else op_coeffs_c128(p.ops[k], reinterpret_cast<double *>(coef.data() + k * per));
+        }
+        const Compiled &c = *fns[i];
+        const uint64_t ntiles = dim(s) >> p.k;
+        const unsigned grid = unsigned(std::min<uint64_t>(ntiles, uint64_t(c.per_sm) * s->num_sms));
+        void *amp = s->amp;
+        void *args[] = {&amp, const_cast<uint64_t *>(&ntiles), coef.data()};
+        prof_bytes(s, QV_K_FUSED, 2.0 * double(dim(s)) * amp_bytes(s->dt));
+        prof_begin(s, QV_K_FUSED);
+        const CUresult r = api().launch(c.fn, grid, 1, 1, 1u << (p.k - kRegBits), 1, 1, unsigned(c.smem),
+                                          reinterpret_cast<CUstream>(s->stream), args, nullptr);
+        prof_end(s, QV_K_FUSED);
+        if (r != CUDA_SUCCESS) return cu_fail(r, "cuLaunchKernel");
+        s->prof.h2d += coef.size() * sizeof(uint64_t);
+    }
+    return QV_OK;
+}
+
+}  // namespace qv

@@ -231,6 +231,10 @@ bool make_plan(int n, int k, bool pin0, bool fuse, const std::vector<PGate> &gat
                     best = q;
                 }
             }
+            if (best < 0) {
+                err = "no qubit left to add to the tile";
+                return false;
+            }
             inS[best] = 1;
         }
         Pass P;

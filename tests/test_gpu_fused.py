@@ -17,27 +17,29 @@ def dist(a, b):
     return float(np.linalg.norm(a.astype(np.complex128) - b))
 
 
-def run_gpu(qv, n, dtype, gates, psi=None, mode=2, tile_bits=0, basis=0):
+def run_gpu(qv, n, dtype, gates, psi=None, mode=2, tile_bits=0, basis=0, flags=0):
     h = qv.qv_create(n, dtype)
     try:
         if psi is not None:
             qv.qv_set_state(h, psi)
         else:
             qv.qv_set_basis(h, basis)
-        qv.qv_apply_circuit(h, gates, mode=mode, tile_bits=tile_bits)
+        qv.qv_apply_circuit(h, gates, mode=mode, tile_bits=tile_bits, flags=flags)
         return qv.qv_get_state(h)
     finally:
         qv.qv_destroy(h)
 
 
+# flags: 0 = compiled passes with gate fusion, 1 = no fusion, 2 = interpreting kernel
+@pytest.mark.parametrize("flags", [0, 1, 2])
 @pytest.mark.parametrize("dtype", [0, 1])
 @pytest.mark.parametrize("n,k", [(10, 10), (11, 10), (11, 11), (12, 12), (13, 10), (13, 12), (16, 11), (17, 12)])
-def test_random_gate_kinds_fused(qvlib, orc, cuda, dtype, n, k):
+def test_random_gate_kinds_fused(qvlib, orc, cuda, dtype, n, k, flags):
     """Every gate kind, random controls (inside and outside the tile), swaps."""
     qv = qvlib
     gates = W.random_gate_list(n, 200, seed=1000 * n + k, ctrl_prob=0.4)
     psi = W.random_state(n, 31 * n + k)
-    got = run_gpu(qv, n, dtype, gates, psi=psi, tile_bits=k)
+    got = run_gpu(qv, n, dtype, gates, psi=psi, tile_bits=k, flags=flags)
     want = orc.run(n, gates, psi.copy())
     assert dist(got, want) <= TOL[dtype]
 
@@ -49,8 +51,9 @@ def test_random_circuit_16q_fused(qvlib, orc, cuda, dtype):
     gates = W.random_circuit(n, 20, W.config_seed(0))
     want = orc.run(n, gates)
     for k in (10, 11, 12):
-        got = run_gpu(qv, n, dtype, gates, tile_bits=k)
-        assert dist(got, want) <= TOL[dtype], k
+        for flags in (0, 2):
+            got = run_gpu(qv, n, dtype, gates, tile_bits=k, flags=flags)
+            assert dist(got, want) <= TOL[dtype], (k, flags)
 
 
 @pytest.mark.parametrize("n", [10, 12, 15])
