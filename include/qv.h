@@ -186,6 +186,28 @@ qv_status qv_expect_z(qv_state *s, const double *weights, double *per_qubit, dou
 /* <psi|H|psi> for H = sum_t terms[t].coeff * P_t. Synchronises. */
 qv_status qv_expect_pauli(qv_state *s, const qv_pauli_term *terms, size_t nt, double *out);
 
+/* out = H |psi> for H = sum_t terms[t].coeff * P_t; `out` is another state of
+ * the same n, dtype and stream (its previous contents are overwritten). */
+qv_status qv_apply_pauli(qv_state *s, const qv_pauli_term *terms, size_t nt, qv_state *out);
+
+/* ------------------------------------------------------------------------ */
+/* Gradients (not in the paper)                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Gradient of E = <psi|H|psi>, psi = U_L ... U_1 psi_0, with respect to the
+ * trainable angles (qv_gate.param) by the adjoint method (Jones and Gacon,
+ * arXiv:2009.02823): a forward pass (fused), lambda = H psi, then a reverse
+ * sweep that per gate un-computes psi <- U^dagger psi, adds 2 Re <lambda|
+ * dU/dtheta psi> for each trainable angle and updates lambda <- U^dagger
+ * lambda, in one pass over both buffers; no intermediate state is stored.
+ * psi_0 is the handle's current state; when the call returns the handle
+ * holds psi_0 again (up to rounding). grad_out[p] sums the derivatives of
+ * every angle with param == p (0 <= p < nparams); trainable angles are
+ * theta[0] of RX, RY, RZ, P and all three of U3. *expval_out (may be NULL)
+ * gets E. Needs one extra state buffer on the device. Synchronises. */
+qv_status qv_adjoint_grad(qv_state *s, const qv_gate *g, size_t ng, const qv_pauli_term *H, size_t nt,
+                          size_t nparams, double *grad_out, double *expval_out);
+
 /* Allocation-free Z sums (the paper has no counterpart; this exists for
  * callers that cannot allocate device memory). Some callers cannot call
  * cudaMalloc at the point where they need a result: code recording a CUDA

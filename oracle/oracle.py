@@ -238,21 +238,43 @@ def _occurrences(gates: Sequence, nparams: int):
     return occ
 
 
-def param_shift_grad(n: int, gates: Sequence, terms, nparams: int) -> np.ndarray:
-    """d<H>/d theta_p by the parameter-shift rule: every trainable angle here
-    enters as exp(-i theta G / 2) with G^2 = I up to a global phase (RX, RY, RZ,
-    P and each angle of U3), so (E(theta + pi/2) - E(theta - pi/2)) / 2 is the
-    exact derivative; a parameter used by several gates sums their terms."""
+_ROTATION_ANGLE = {"rx": (0,), "ry": (0,), "rz": (0,), "u3": (0,)}
+_D1 = (math.sqrt(2.0) + 1.0) / (4.0 * math.sqrt(2.0))
+_D2 = (math.sqrt(2.0) - 1.0) / (4.0 * math.sqrt(2.0))
+
+
+def param_shift_grad(n: int, gates: Sequence, terms, nparams: int, psi0: np.ndarray | None = None) -> np.ndarray:
+    """d<H>/d theta_p by parameter-shift rules, summed over every gate using p
+    (circuit started from psi0, default |0...0>).
+
+    Each angle enters the circuit as exp(-i theta G) for a fixed generator G.
+    When the eigenvalues of G differ only by 0 or 1 -- any uncontrolled angle
+    here (RX, RY, RZ, P, U3 up to a global phase), and a controlled P or the
+    phi / lambda angles of a controlled U3, whose generator is a projector --
+    E(theta) is a + b cos(theta) + c sin(theta) and
+        dE = (E(theta + pi/2) - E(theta - pi/2)) / 2
+    is exact. A controlled rotation angle (RX, RY, RZ, U3 theta with a control)
+    has G = |1><1| (x) sigma/2 with eigenvalues {-1/2, 0, 1/2}: E then holds
+    frequencies 1/2 and 1, and the four-term rule
+        dE = d1 (E(+pi/2) - E(-pi/2)) - d2 (E(+3pi/2) - E(-3pi/2)),
+        d1 = (sqrt 2 + 1) / (4 sqrt 2), d2 = (sqrt 2 - 1) / (4 sqrt 2)
+    is exact (it reproduces d/dtheta of sin(w theta) for w = 1/2 and 1 and
+    annihilates the cosines; Wierichs et al., "General parameter-shift rules
+    for quantum gradients", Quantum 6, 677 (2022))."""
     g = np.zeros(nparams)
     for p, uses in enumerate(_occurrences(gates, nparams)):
         for gi, slot in uses:
-            ep = energy(n, _shifted(gates, gi, slot, math.pi / 2), terms)
-            em = energy(n, _shifted(gates, gi, slot, -math.pi / 2), terms)
-            g[p] += 0.5 * (ep - em)
+            gt = gates[gi]
+            E = lambda d: energy(n, _shifted(gates, gi, slot, d), terms, psi0)
+            if gt.ctrl >= 0 and slot in _ROTATION_ANGLE.get(gt.kind, ()):
+                g[p] += _D1 * (E(math.pi / 2) - E(-math.pi / 2)) - _D2 * (E(1.5 * math.pi) - E(-1.5 * math.pi))
+            else:
+                g[p] += 0.5 * (E(math.pi / 2) - E(-math.pi / 2))
     return g
 
 
-def finite_diff_grad(n: int, gates: Sequence, terms, nparams: int, h: float = 1e-3) -> np.ndarray:
+def finite_diff_grad(n: int, gates: Sequence, terms, nparams: int, h: float = 1e-3,
+                     psi0: np.ndarray | None = None) -> np.ndarray:
     """Central differences (E(theta_p + h) - E(theta_p - h)) / (2h), shifting
     every gate that uses parameter p together."""
     g = np.zeros(nparams)
@@ -263,5 +285,5 @@ def finite_diff_grad(n: int, gates: Sequence, terms, nparams: int, h: float = 1e
         for gi, slot in uses:
             gp = _shifted(gp, gi, slot, h)
             gm = _shifted(gm, gi, slot, -h)
-        g[p] = (energy(n, gp, terms) - energy(n, gm, terms)) / (2 * h)
+        g[p] = (energy(n, gp, terms, psi0) - energy(n, gm, terms, psi0)) / (2 * h)
     return g

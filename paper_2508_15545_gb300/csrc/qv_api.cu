@@ -201,6 +201,7 @@ qv_status qv_destroy(qv_state *s)
     if (!s) return QV_OK;
     cudaError_t e = cudaStreamSynchronize(s->stream);
     plan_cache_release(s);
+    adjoint_release(s);
     prof_release(s);
     if (s->scratch.ptr) cudaFree(s->scratch.ptr);
     if (s->host_out) cudaFreeHost(s->host_out);
@@ -356,6 +357,46 @@ qv_status qv_expect_pauli(qv_state *s, const qv_pauli_term *terms, size_t nt, do
     for (size_t k = 0; k < nt; ++k)
         if ((terms[k].xmask | terms[k].zmask) & ~lim) return fail(QV_ERR_ARG, "term %zu acts on a qubit >= n", k);
     return reduce_pauli(s, terms, nt, out);
+}
+
+qv_status qv_apply_pauli(qv_state *s, const qv_pauli_term *terms, size_t nt, qv_state *out)
+{
+    CHECK_HANDLE(s);
+    if (!out) return fail(QV_ERR_ARG, "out is NULL");
+    if (out == s || out->amp == s->amp) return fail(QV_ERR_ARG, "out must be a different buffer");
+    if (out->n != s->n || out->dt != s->dt) return fail(QV_ERR_ARG, "out must have the same n and dtype");
+    if (out->stream != s->stream) return fail(QV_ERR_ARG, "out must use the same stream");
+    if (nt && !terms) return fail(QV_ERR_ARG, "terms is NULL");
+    const uint64_t lim = (uint64_t(1) << s->n) - 1;
+    for (size_t k = 0; k < nt; ++k)
+        if ((terms[k].xmask | terms[k].zmask) & ~lim) return fail(QV_ERR_ARG, "term %zu acts on a qubit >= n", k);
+    return pauli_apply(s, s->amp, out->amp, terms, nt);
+}
+
+qv_status qv_adjoint_grad(qv_state *s, const qv_gate *g, size_t ng, const qv_pauli_term *H, size_t nt,
+                          size_t nparams, double *grad_out, double *expval_out)
+{
+    CHECK_HANDLE(s);
+    if (ng && !g) return fail(QV_ERR_ARG, "gate list is NULL");
+    if (nt && !H) return fail(QV_ERR_ARG, "terms is NULL");
+    if (nparams && !grad_out) return fail(QV_ERR_ARG, "grad_out is NULL");
+    const uint64_t lim = (uint64_t(1) << s->n) - 1;
+    for (size_t k = 0; k < nt; ++k)
+        if ((H[k].xmask | H[k].zmask) & ~lim) return fail(QV_ERR_ARG, "term %zu acts on a qubit >= n", k);
+    for (size_t l = 0; l < ng; ++l) {
+        QV_TRY(validate_gate(g[l], s->n, l));
+        const qv_gate &G = g[l];
+        const int nangles = G.kind == QV_G_U3 ? 3 : (G.kind == QV_G_RX || G.kind == QV_G_RY || G.kind == QV_G_RZ ||
+                                                     G.kind == QV_G_P) ? 1 : 0;
+        for (int a = 0; a < 3; ++a) {
+            if (G.param[a] < -1) return fail(QV_ERR_ARG, "gate %zu: bad parameter index %d", l, G.param[a]);
+            if (G.param[a] >= 0 && a >= nangles)
+                return fail(QV_ERR_ARG, "gate %zu: angle %d of this gate kind is not trainable", l, a);
+            if (G.param[a] >= 0 && size_t(G.param[a]) >= nparams)
+                return fail(QV_ERR_ARG, "gate %zu: parameter index %d >= nparams", l, G.param[a]);
+        }
+    }
+    return adjoint_grad(s, g, ng, H, nt, nparams, grad_out, expval_out);
 }
 
 const char *qv_last_error(void) { return g_err; }

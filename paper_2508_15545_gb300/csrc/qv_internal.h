@@ -35,7 +35,8 @@ struct Prof {
     uint64_t h2d = 0, d2h = 0;
 };
 
-struct PlanCache;  // fused-pass buffers (fused.cu)
+struct PlanCache;       // fused-pass buffers (fused.cu)
+struct AdjointBuffers;  // lambda buffer and gradient partials (adjoint.cu)
 
 }  // namespace qv
 
@@ -52,6 +53,7 @@ struct qv_state {
     size_t host_out_len = 0;
     qv::Prof prof;
     qv::PlanCache *plan = nullptr;
+    qv::AdjointBuffers *adj = nullptr;
 };
 
 namespace qv {
@@ -114,6 +116,17 @@ qv_status launch_diag(qv_state *s, int t, int ctrl, cd d0, cd d1);
 qv_status launch_swap(qv_state *s, int a, int b);
 // out[pi(i)] = in[i]; out and in distinct buffers of the same size.
 qv_status launch_permute(qv_state *s, const void *in, void *out, const int32_t *perm);
+
+// One gate through the per-gate kernels (qv_api.cu).
+qv_status apply_gate_plain(qv_state *s, const qv_gate &g);
+qv_status validate_gate(const qv_gate &g, int n, size_t idx);
+
+// ---------------------------------------------------------------- adjoint (adjoint.cu)
+// dst = H src for H = sum of Pauli terms; src, dst: 2^n amplitudes of s's dtype.
+qv_status pauli_apply(qv_state *s, const void *src, void *dst, const qv_pauli_term *terms, size_t nt);
+qv_status adjoint_grad(qv_state *s, const qv_gate *g, size_t ng, const qv_pauli_term *H, size_t nt, size_t nparams,
+                       double *grad_out, double *expval_out);
+void adjoint_release(qv_state *s);
 
 // ---------------------------------------------------------------- reductions (reduce_kernels.cu)
 // out[0] = sum |a|^2, out[1 + q] = sum over bit q set of |a|^2, q < n.

@@ -11,8 +11,7 @@ namespace qv {
 bool fused_supported(const qv_state *s, const qv_plan_opts *opts);
 qv_status apply_fused(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_opts *opts);
 qv_status plan_info(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t out[4]);
-// Validates one gate for an n-qubit state (gate index `idx` for messages).
-qv_status validate_gate(const qv_gate &g, int n, size_t idx);
+
 // Bit q of every index moves to bit perm[q].
 qv_status apply_permutation(qv_state *s, const int32_t *perm);
 // Frees per-handle planning buffers.

@@ -87,6 +87,9 @@ def _load():
         "qv_expect_z": [_H, P, P, ctypes.POINTER(ctypes.c_double)],
         "qv_expect_pauli": [_H, ctypes.POINTER(qv_pauli_term), ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)],
         "qv_zsums_noalloc": [P, ctypes.c_int, ctypes.c_int, P, P],
+        "qv_apply_pauli": [_H, ctypes.POINTER(qv_pauli_term), ctypes.c_size_t, _H],
+        "qv_adjoint_grad": [_H, ctypes.POINTER(qv_gate), ctypes.c_size_t, ctypes.POINTER(qv_pauli_term),
+                            ctypes.c_size_t, ctypes.c_size_t, P, ctypes.POINTER(ctypes.c_double)],
         "qv_profile": [_H, ctypes.c_int],
         "qv_profile_read": [_H, ctypes.POINTER(qv_kernel_stat), ctypes.c_int],
         "qv_transfer_bytes": [_H, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
@@ -271,6 +274,25 @@ def qv_expect_pauli(h: int, terms: Sequence[Tuple[float, int, int]]) -> float:
     out = ctypes.c_double()
     _check(lib.qv_expect_pauli(h, terms_to_c(terms), len(terms), ctypes.byref(out)))
     return out.value
+
+
+def qv_apply_pauli(h: int, terms, out_h: int):
+    """out_h <- H |psi_h> (same n, dtype and stream)."""
+    _check(lib.qv_apply_pauli(h, terms_to_c(terms), len(terms), out_h))
+
+
+def qv_adjoint_grad(h: int, gates, terms, nparams: int):
+    """Adjoint-method gradient of <H> over the circuit ``gates`` applied to the
+    handle's current state. Returns (grad as numpy array, <H>)."""
+    if isinstance(gates, tuple) and len(gates) == 2 and isinstance(gates[1], int):
+        arr, ng = gates
+    else:
+        arr, ng = gates_to_c(gates), len(gates)
+    grad = np.zeros(max(1, nparams))
+    e = ctypes.c_double()
+    _check(lib.qv_adjoint_grad(h, arr, ng, terms_to_c(terms), len(terms), nparams, grad.ctypes.data,
+                               ctypes.byref(e)))
+    return grad[:nparams], e.value
 
 
 def qv_zsums_noalloc(dev_amp: int, n: int, dtype: int, stream, dev_out: int):

@@ -1,0 +1,115 @@
+"""Adjoint gradient and H|psi> against the oracle: gradients by the exact
+parameter-shift rule and central differences (re-simulation only), H|psi> by
+the oracle's Pauli-sum apply."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2508_15545_gb300 import workloads as W
+from paper_2508_15545_gb300.workloads import Gate
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("n", [3, 8, 13])
+def test_apply_pauli_sum(qvlib, orc, cuda, dtype, n):
+    qv = qvlib
+    terms = W.ansatz_hamiltonian(n) + [(0.3, (1 << n) - 1, 0), (-0.7, 0b101, 0b110), (0.25, 0, (1 << n) - 1)]
+    psi = W.random_state(n, 11 + n)
+    a = qv.qv_create(n, dtype)
+    b = qv.qv_create(n, dtype)
+    qv.qv_set_state(a, psi)
+    qv.qv_apply_pauli(a, terms, b)
+    got = qv.qv_get_state(b)
+    ref = psi.astype(np.complex64).astype(np.complex128) if dtype == 0 else psi
+    want = orc.apply_pauli_sum(ref, terms)
+    tol = 2e-5 if dtype == 0 else 1e-12
+    assert np.max(np.abs(got - want)) <= tol * len(terms)
+    qv.qv_destroy(a)
+    qv.qv_destroy(b)
+
+
+def _adjoint(qv, n, dtype, gates, terms, npar, psi0=None):
+    h = qv.qv_create(n, dtype)
+    if psi0 is not None:
+        qv.qv_set_state(h, psi0)
+    before = qv.qv_get_state(h)
+    g, e = qv.qv_adjoint_grad(h, gates, terms, npar)
+    after = qv.qv_get_state(h)
+    qv.qv_destroy(h)
+    return g, e, before, after
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_adjoint_mixed_gates(qvlib, orc, cuda, dtype):
+    """U3 (three trainable angles), RX/RY/RZ/P, controlled parametrised gates,
+    a shared parameter, a SWAP and fixed gates."""
+    qv = qvlib
+    n = 6
+    gates = [Gate("h", 0), Gate("u3", 1, theta=(0.4, 0.9, -0.3), param=(0, 1, 2)),
+             Gate("x", 2, ctrl=1), Gate("rx", 3, theta=(0.6, 0, 0), param=(3, -1, -1)),
+             Gate("rx", 4, theta=(0.6, 0, 0), param=(3, -1, -1)), Gate("swap", 0, target2=5),
+             Gate("p", 2, ctrl=4, theta=(1.3, 0, 0), param=(4, -1, -1)),
+             Gate("ry", 5, ctrl=0, theta=(-0.8, 0, 0), param=(5, -1, -1)),
+             Gate("rz", 0, theta=(0.2, 0, 0), param=(6, -1, -1)), Gate("z", 3, ctrl=2),
+             Gate("u3", 4, ctrl=3, theta=(1.1, -0.2, 0.7), param=(7, 8, -1))]
+    terms = W.ansatz_hamiltonian(n) + [(0.4, 0b011, 0b010), (-0.3, 0, 0b110001)]
+    psi0 = W.random_state(n, 3)
+    g, e, before, after = _adjoint(qv, n, dtype, gates, terms, 9, psi0)
+    want_e = orc.energy(n, gates, terms, psi0)
+    ref = orc.param_shift_grad(n, gates, terms, 9, psi0)
+    tol = 1e-4 if dtype == 0 else 1e-10
+    assert e == pytest.approx(want_e, abs=tol)
+    assert np.max(np.abs(g - ref)) <= tol, (g, ref)
+    # the handle holds psi0 again
+    assert np.linalg.norm(after.astype(complex) - before.astype(complex)) <= (1e-5 if dtype == 0 else 1e-12)
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_adjoint_ansatz_12q_vs_param_shift_and_fd(qvlib, orc, cuda, dtype):
+    """12-qubit copy of the 26-qubit gradient workload: 16 layers of RY, RZ and
+    a CZ ring (384 parameters), H = sum Z_i Z_i+1 + 0.5 sum X_i."""
+    qv = qvlib
+    n, layers = 12, 16
+    gates, npar = W.ansatz_circuit(n, layers, W.config_seed(3, 1))
+    terms = W.ansatz_hamiltonian(n)
+    g, e, _, _ = _adjoint(qv, n, dtype, gates, terms, npar)
+    ps = orc.param_shift_grad(n, gates, terms, npar)
+    fd = orc.finite_diff_grad(n, gates, terms, npar, h=1e-3)
+    l1 = sum(abs(c) for c, _, _ in terms)
+    assert np.max(np.abs(ps - fd)) <= 1e-6 * l1
+    tol = 1e-4 if dtype == 0 else 1e-9
+    assert np.max(np.abs(g - ps)) <= tol
+    assert e == pytest.approx(orc.energy(n, gates, terms), abs=tol)
+
+
+def test_autograd_function(qvlib, orc, cuda):
+    torch = cuda
+    from paper_2508_15545_gb300.autograd import Expectation, expectation
+    n, layers = 10, 3
+    gates, npar = W.ansatz_circuit(n, layers, W.config_seed(3, 2))
+    terms = W.ansatz_hamiltonian(n)
+    model = Expectation(n, gates, terms, npar)
+    p0 = np.array([g.theta[0] for g in gates if g.param[0] >= 0])
+    order = [g.param[0] for g in gates if g.param[0] >= 0]
+    params = torch.zeros(npar, dtype=torch.float64)
+    params[order] = torch.tensor(p0)
+    params.requires_grad_(True)
+    e = expectation(params, model)
+    e.backward()
+    ps = orc.param_shift_grad(n, gates, terms, npar)
+    assert float(e.detach()) == pytest.approx(orc.energy(n, gates, terms), abs=1e-5)
+    assert np.max(np.abs(params.grad.numpy() - ps)) <= 1e-4
+    model.close()
+
+
+def test_adjoint_rejects_bad_params(qvlib, cuda):
+    qv = qvlib
+    h = qv.qv_create(4, 0)
+    with pytest.raises(qv.QvError):
+        qv.qv_adjoint_grad(h, [Gate("h", 0, param=(0, -1, -1))], [(1.0, 0, 1)], 1)
+    with pytest.raises(qv.QvError):
+        qv.qv_adjoint_grad(h, [Gate("ry", 0, param=(3, -1, -1))], [(1.0, 0, 1)], 2)
+    qv.qv_destroy(h)

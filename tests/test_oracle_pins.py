@@ -334,6 +334,24 @@ def test_gradient_u3_and_shared_parameter(orc):
     assert np.allclose(ps, fd, atol=1e-6)
 
 
+def test_gradient_controlled_rotations_ps_vs_fd(orc):
+    """Controlled rotations (generator eigenvalues -1/2, 0, 1/2) need the
+    four-term shift rule; controlled phases and U3's phi / lambda do not."""
+    n = 4
+    gates = [Gate("h", 0), Gate("h", 2),
+             Gate("ry", 1, ctrl=0, theta=(0.7, 0, 0), param=(0, -1, -1)),
+             Gate("rx", 3, ctrl=2, theta=(-1.2, 0, 0), param=(1, -1, -1)),
+             Gate("rz", 2, ctrl=1, theta=(0.4, 0, 0), param=(2, -1, -1)),
+             Gate("u3", 0, ctrl=3, theta=(1.1, -0.2, 0.7), param=(3, 4, 5)),
+             Gate("p", 3, ctrl=0, theta=(0.9, 0, 0), param=(6, -1, -1)),
+             Gate("h", 1)]
+    terms = W.ansatz_hamiltonian(n) + [(0.5, 0b0101, 0b0011)]
+    ps = orc.param_shift_grad(n, gates, terms, 7)
+    fd = orc.finite_diff_grad(n, gates, terms, 7, h=1e-4)
+    assert np.max(np.abs(ps - fd)) <= 1e-7
+    assert np.max(np.abs(ps)) > 1e-2
+
+
 def test_gradient_ansatz_ps_vs_fd(orc):
     n, layers = 4, 2
     gates, npar = W.ansatz_circuit(n, layers, seed=W.config_seed(3, 1))
