@@ -165,6 +165,14 @@ qv_status qv_apply_circuit(qv_state *s, const qv_gate *g, size_t ng, const qv_pl
  * operations. Host only. */
 qv_status qv_plan_info(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t out[4]);
 
+/* Autotuner: runs g[0..ng) in fused mode with every supported tile size
+ * (2^10 .. 2^12 amplitudes, at most 2^n), times each with CUDA events after a
+ * warm-up run, and remembers the fastest for this (n, dtype, engine) -- later
+ * fused calls, batches and plans with tile_bits = 0 use it. opts selects the
+ * engine (QV_PLAN_INTERPRET) and fusion flags; *best_tile_bits gets the
+ * winner. Overwrites the state (it is |0...0> on return). Synchronises. */
+qv_status qv_autotune(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t *best_tile_bits);
+
 /* Reorders qubits: bit q of every amplitude index moves to bit perm[q]
  * (out[pi(i)] = in[i]). perm is a permutation of 0..n-1. In place. */
 qv_status qv_permute_qubits(qv_state *s, const int32_t *perm);
@@ -270,6 +278,39 @@ qv_status qv_profile_read(qv_state *s, qv_kernel_stat *out, int count);
 /* Bytes the library copied host->device and device->host since the last
  * qv_profile reset (gate programs, results; not qv_get/set_state). */
 qv_status qv_transfer_bytes(qv_state *s, uint64_t *h2d, uint64_t *d2h);
+
+/* ------------------------------------------------------------------------ */
+/* Batches (not in the paper)                                                 */
+/* ------------------------------------------------------------------------ */
+
+typedef struct qv_batch qv_batch;   /* opaque */
+
+/* One member of a batch: a state and the circuit to run on it. */
+typedef struct {
+    qv_state *state;
+    const qv_gate *gates;
+    size_t ngates;
+} qv_batch_item;
+
+/* Plans every circuit (fused passes; tile size per qubit count from the
+ * autotuner unless opts->tile_bits is set; all states must have the same
+ * dtype, n >= 10, and be distinct), uploads the pass programs, and captures
+ * one CUDA graph that sets every state to |0...0>, runs all circuits in one
+ * persistent launch per tile size -- CTAs claim (circuit, pass, tile chunk)
+ * work items from an atomic counter in round order and wait (bounded) on a
+ * per-pass completion counter before a circuit's next pass -- and, when nt > 0,
+ * reduces <H> for every state. The gate lists are copied; the states must
+ * outlive the batch. */
+qv_status qv_batch_create(const qv_batch_item *items, size_t count, const qv_pauli_term *H, size_t nt,
+                          const qv_plan_opts *opts, qv_batch **out);
+
+/* Replays the batch's graph on its own stream (after synchronising the
+ * states' streams) and waits for it. expvals[count] (may be NULL) gets <H>
+ * per state when the batch has a Hamiltonian. QV_ERR_TIMEOUT if a
+ * dependency wait in the persistent launch gave up. */
+qv_status qv_batch_run(qv_batch *b, double *expvals);
+
+qv_status qv_batch_destroy(qv_batch *b);
 
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *qv_last_error(void);

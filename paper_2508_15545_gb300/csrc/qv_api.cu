@@ -399,6 +399,52 @@ qv_status qv_adjoint_grad(qv_state *s, const qv_gate *g, size_t ng, const qv_pau
     return adjoint_grad(s, g, ng, H, nt, nparams, grad_out, expval_out);
 }
 
+qv_status qv_autotune(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t *best_tile_bits)
+{
+    CHECK_HANDLE(s);
+    if (ng && !g) return fail(QV_ERR_ARG, "gate list is NULL");
+    for (size_t k = 0; k < ng; ++k) QV_TRY(validate_gate(g[k], s->n, k));
+    return autotune(s, g, ng, opts, best_tile_bits);
+}
+
+qv_status qv_batch_create(const qv_batch_item *items, size_t count, const qv_pauli_term *H, size_t nt,
+                          const qv_plan_opts *opts, qv_batch **out)
+{
+    if (!out) return fail(QV_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!items || count == 0) return fail(QV_ERR_ARG, "empty batch");
+    if (count > 65535) return fail(QV_ERR_ARG, "batch of %zu circuits exceeds 65535", count);
+    if (nt && !H) return fail(QV_ERR_ARG, "terms is NULL");
+    std::vector<const qv_state *> seen;
+    for (size_t c = 0; c < count; ++c) {
+        const qv_state *s = items[c].state;
+        if (!s) return fail(QV_ERR_ARG, "batch item %zu: NULL state", c);
+        if (s->dt != items[0].state->dt) return fail(QV_ERR_ARG, "batch item %zu: dtype differs", c);
+        if (s->device != items[0].state->device) return fail(QV_ERR_ARG, "batch item %zu: other device", c);
+        for (const qv_state *o : seen)
+            if (o == s || o->amp == s->amp) return fail(QV_ERR_ARG, "batch item %zu: state used twice", c);
+        seen.push_back(s);
+        if (items[c].ngates && !items[c].gates) return fail(QV_ERR_ARG, "batch item %zu: gate list is NULL", c);
+        for (size_t k = 0; k < items[c].ngates; ++k) QV_TRY(validate_gate(items[c].gates[k], s->n, k));
+        const uint64_t lim = (uint64_t(1) << s->n) - 1;
+        for (size_t k = 0; k < nt; ++k)
+            if ((H[k].xmask | H[k].zmask) & ~lim) return fail(QV_ERR_ARG, "term %zu acts on a qubit >= n of item %zu", k, c);
+    }
+    return batch_create(items, count, H, nt, opts, out);
+}
+
+qv_status qv_batch_run(qv_batch *b, double *expvals)
+{
+    if (!b) return fail(QV_ERR_ARG, "NULL batch");
+    return batch_run(b, expvals);
+}
+
+qv_status qv_batch_destroy(qv_batch *b)
+{
+    batch_release(b);
+    return QV_OK;
+}
+
 const char *qv_last_error(void) { return g_err; }
 
 }  // extern "C"

@@ -3,6 +3,9 @@
 // permutations.
 #pragma once
 
+#include <vector>
+
+#include "planner.h"
 #include "qv_internal.h"
 
 namespace qv {
@@ -16,5 +19,19 @@ qv_status plan_info(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_pl
 qv_status apply_permutation(qv_state *s, const int32_t *perm);
 // Frees per-handle planning buffers.
 void plan_cache_release(qv_state *s);
+// qv_gate list -> planner gates (matrices in FP64, classified).
+qv_status to_pgates(const qv_gate *g, size_t ng, std::vector<plan::PGate> &out);
+
+// ---- autotuner (autotune.cu)
+// Tile bits to use by default: the autotuned value for (n, dtype, engine) when
+// one was measured, else min(n, 12).
+int tuned_tile_bits(int n, qv_dtype dt, bool interpreting = true);
+qv_status autotune(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t *best_out);
+
+// ---- batched circuits (batch.cu)
+qv_status batch_create(const qv_batch_item *items, size_t count, const qv_pauli_term *H, size_t nt,
+                       const qv_plan_opts *opts, qv_batch **out);
+qv_status batch_run(qv_batch *b, double *expvals);
+void batch_release(qv_batch *b);
 
 }  // namespace qv

@@ -61,6 +61,10 @@ class qv_pauli_term(ctypes.Structure):
 _H = ctypes.c_void_p  # qv_state*
 
 
+class qv_batch_item(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_void_p), ("gates", ctypes.POINTER(qv_gate)), ("ngates", ctypes.c_size_t)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError("libqv.so not built (run paper_2508_15545_gb300.build.build()); "
@@ -90,6 +94,12 @@ def _load():
         "qv_apply_pauli": [_H, ctypes.POINTER(qv_pauli_term), ctypes.c_size_t, _H],
         "qv_adjoint_grad": [_H, ctypes.POINTER(qv_gate), ctypes.c_size_t, ctypes.POINTER(qv_pauli_term),
                             ctypes.c_size_t, ctypes.c_size_t, P, ctypes.POINTER(ctypes.c_double)],
+        "qv_autotune": [_H, ctypes.POINTER(qv_gate), ctypes.c_size_t, ctypes.POINTER(qv_plan_opts),
+                        ctypes.POINTER(ctypes.c_int32)],
+        "qv_batch_create": [ctypes.POINTER(qv_batch_item), ctypes.c_size_t, ctypes.POINTER(qv_pauli_term),
+                            ctypes.c_size_t, ctypes.POINTER(qv_plan_opts), ctypes.POINTER(ctypes.c_void_p)],
+        "qv_batch_run": [ctypes.c_void_p, P],
+        "qv_batch_destroy": [ctypes.c_void_p],
         "qv_profile": [_H, ctypes.c_int],
         "qv_profile_read": [_H, ctypes.POINTER(qv_kernel_stat), ctypes.c_int],
         "qv_transfer_bytes": [_H, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
@@ -299,6 +309,59 @@ def qv_zsums_noalloc(dev_amp: int, n: int, dtype: int, stream, dev_out: int):
     """Allocation-free Z sums into the caller's device buffer of n + 1 doubles
     (see include/qv.h); asynchronous on ``stream``."""
     _check(lib.qv_zsums_noalloc(dev_amp, n, dtype, _stream_ptr(stream), dev_out))
+
+
+def qv_autotune(h: int, gates, flags: int = 0) -> int:
+    """Times the fused path for every tile size on this circuit, remembers the
+    fastest for (n, dtype, engine) and returns it. Leaves the state at |0...0>."""
+    arr, ng = _gate_array(gates)
+    opts = plan_opts(QV_MODE_FUSED, 0, flags)
+    best = ctypes.c_int32()
+    _check(lib.qv_autotune(h, arr, ng, ctypes.byref(opts), ctypes.byref(best)))
+    return best.value
+
+
+class Batch:
+    """qv_batch_create / qv_batch_run / qv_batch_destroy: many (state, circuit)
+    pairs in one graph-captured persistent launch, plus <H> per state."""
+
+    def __init__(self, items, terms=None, tile_bits: int = 0, flags: int = 0):
+        self.count = len(items)
+        arrs = [_gate_array(g) for _, g in items]
+        c_items = (qv_batch_item * self.count)()
+        for k, ((h, _), (arr, ng)) in enumerate(zip(items, arrs)):
+            c_items[k].state = h
+            c_items[k].gates = ctypes.cast(arr, ctypes.POINTER(qv_gate))
+            c_items[k].ngates = ng
+        terms = list(terms or [])
+        opts = plan_opts(QV_MODE_FUSED, tile_bits, flags)
+        b = ctypes.c_void_p()
+        _check(lib.qv_batch_create(c_items, self.count, terms_to_c(terms), len(terms), ctypes.byref(opts),
+                                   ctypes.byref(b)))
+        self.b = b.value
+        self.has_h = len(terms) > 0
+
+    def run(self) -> np.ndarray:
+        out = np.zeros(self.count)
+        _check(lib.qv_batch_run(self.b, out.ctypes.data if self.has_h else None))
+        return out
+
+    def close(self):
+        if self.b:
+            _check(lib.qv_batch_destroy(self.b))
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _gate_array(gates):
+    if isinstance(gates, tuple) and len(gates) == 2 and isinstance(gates[1], int):
+        return gates
+    return gates_to_c(gates), len(gates)
 
 
 def qv_profile(h: int, timing: bool = False):
