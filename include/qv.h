@@ -216,6 +216,13 @@ qv_status qv_apply_pauli(qv_state *s, const qv_pauli_term *terms, size_t nt, qv_
 qv_status qv_adjoint_grad(qv_state *s, const qv_gate *g, size_t ng, const qv_pauli_term *H, size_t nt,
                           size_t nparams, double *grad_out, double *expval_out);
 
+/* Distance of the state to the closed form of the quantum Fourier transform
+ * of the basis state |j> (the paper's workloads have no QFT; this checks large
+ * runs on the GPU): *dist = sqrt( sum_k |a_k - exp(2 pi i (j k mod 2^n) / 2^n)
+ * / 2^(n/2)|^2 ). The phase index is exact integer arithmetic; the reference
+ * amplitudes come from FP64 sincospi tables; sums are FP64. Synchronises. */
+qv_status qv_verify_qft(qv_state *s, uint64_t j, double *dist);
+
 /* Allocation-free Z sums (the paper has no counterpart; this exists for
  * callers that cannot allocate device memory). Some callers cannot call
  * cudaMalloc at the point where they need a result: code recording a CUDA

@@ -445,6 +445,14 @@ qv_status qv_batch_destroy(qv_batch *b)
     return QV_OK;
 }
 
+qv_status qv_verify_qft(qv_state *s, uint64_t j, double *dist)
+{
+    CHECK_HANDLE(s);
+    if (!dist) return fail(QV_ERR_ARG, "dist is NULL");
+    if (j >= dim(s)) return fail(QV_ERR_ARG, "basis index out of range");
+    return verify_qft(s, j, dist);
+}
+
 const char *qv_last_error(void) { return g_err; }
 
 }  // extern "C"

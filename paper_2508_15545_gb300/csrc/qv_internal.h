@@ -128,6 +128,9 @@ qv_status adjoint_grad(qv_state *s, const qv_gate *g, size_t ng, const qv_pauli_
                        double *grad_out, double *expval_out);
 void adjoint_release(qv_state *s);
 
+// ---------------------------------------------------------------- verification (verify.cu)
+qv_status verify_qft(qv_state *s, uint64_t j, double *dist);
+
 // ---------------------------------------------------------------- reductions (reduce_kernels.cu)
 // out[0] = sum |a|^2, out[1 + q] = sum over bit q set of |a|^2, q < n.
 qv_status reduce_zsums(qv_state *s, double *out_host);

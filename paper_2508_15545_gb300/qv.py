@@ -100,6 +100,7 @@ def _load():
                             ctypes.c_size_t, ctypes.POINTER(qv_plan_opts), ctypes.POINTER(ctypes.c_void_p)],
         "qv_batch_run": [ctypes.c_void_p, P],
         "qv_batch_destroy": [ctypes.c_void_p],
+        "qv_verify_qft": [_H, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)],
         "qv_profile": [_H, ctypes.c_int],
         "qv_profile_read": [_H, ctypes.POINTER(qv_kernel_stat), ctypes.c_int],
         "qv_transfer_bytes": [_H, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
@@ -362,6 +363,13 @@ def _gate_array(gates):
     if isinstance(gates, tuple) and len(gates) == 2 and isinstance(gates[1], int):
         return gates
     return gates_to_c(gates), len(gates)
+
+
+def qv_verify_qft(h: int, j: int) -> float:
+    """||psi - QFT|j>||_2 from the closed form, computed on the GPU."""
+    d = ctypes.c_double()
+    _check(lib.qv_verify_qft(h, j, ctypes.byref(d)))
+    return d.value
 
 
 def qv_profile(h: int, timing: bool = False):

@@ -1,0 +1,82 @@
+"""Closed-form QFT check on the GPU, the uneven random-circuit batch, and the
+33-qubit (64 GiB) QFT."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2508_15545_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("n", [10, 13])
+def test_verify_qft_matches_numpy_distance(qvlib, cuda, dtype, n):
+    """The GPU distance equals the distance numpy computes from the fetched state."""
+    qv = qvlib
+    N = 1 << n
+    h = qv.qv_create(n, dtype)
+    for j in (0, 5, N - 1):
+        qv.qv_set_basis(h, j)
+        qv.qv_apply_circuit(h, W.qft_circuit(n))
+        psi = qv.qv_get_state(h).astype(complex)
+        k = np.arange(N)
+        ref = np.exp(2j * np.pi * ((j * k) % N) / N) / math.sqrt(N)
+        want = float(np.linalg.norm(psi - ref))
+        got = qv.qv_verify_qft(h, j)
+        assert got == pytest.approx(want, abs=1e-9)
+        assert got <= (1e-5 if dtype == 0 else 1e-12)
+        # a wrong j is far away
+        assert qv.qv_verify_qft(h, (j + 1) % N) > 0.5
+    qv.qv_destroy(h)
+
+
+def test_qft_33_qubits_closed_form(qvlib, cuda):
+    """33-qubit complex64 QFT of a random basis state (64 GiB), fused passes."""
+    qv = qvlib
+    torch = cuda
+    free, _ = torch.cuda.mem_get_info()
+    n = 33
+    if free < (8 << n) + (4 << 30):
+        pytest.skip("needs 68 GiB of free device memory")
+    j = int(W.SplitMix64(W.config_seed(4, 99)).integers(0, (1 << n) - 1, 1)[0])
+    h = qv.qv_create(n, 0)
+    qv.qv_set_basis(h, j)
+    qv.qv_apply_circuit(h, W.qft_circuit(n))
+    d = qv.qv_verify_qft(h, j)
+    nrm = qv.qv_norm2(h)
+    qv.qv_destroy(h)
+    assert d <= 1e-5
+    # complex64 rounds 1/sqrt(2) down by ~1.6e-8 relative; 33 Hadamards per
+    # amplitude leave ||psi||^2 about 1e-6 low, within the 1e-5 state bound
+    assert nrm == pytest.approx(1.0, abs=1e-5)
+
+
+def test_uneven_batch_64_circuits(qvlib, orc, cuda):
+    """64 random circuits, qubits uniform in [16, 28], depth uniform in [10, 60],
+    one persistent launch per tile size. Circuits up to 20 qubits are checked
+    against the oracle; all of them against the per-gate GPU path and the norm."""
+    qv = qvlib
+    spec = W.uneven_batch(64, W.config_seed(4))
+    circuits = [W.random_circuit(n, d, seed) for n, d, seed in spec]
+    states = [qv.qv_create(n, 0) for n, _, _ in spec]
+    b = qv.Batch(list(zip(states, circuits)))
+    b.run()
+    checked = 0
+    for (n, d, seed), h, g in zip(spec, states, circuits):
+        got = qv.qv_get_state(h)
+        if n <= 20:
+            assert np.linalg.norm(got.astype(complex) - orc.run(n, g)) <= 1e-5, (n, d)
+            checked += 1
+        else:
+            p = qv.qv_create(n, 0)
+            qv.qv_apply_circuit(p, g, mode=qv.QV_MODE_PLAIN)
+            ref = qv.qv_get_state(p)
+            qv.qv_destroy(p)
+            assert np.linalg.norm(got.astype(complex) - ref.astype(complex)) <= 1e-4, (n, d)
+        assert qv.qv_norm2(h) == pytest.approx(1.0, abs=1e-5)
+    assert checked >= 10
+    b.close()
+    for h in states:
+        qv.qv_destroy(h)
