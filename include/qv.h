@@ -223,6 +223,11 @@ qv_status qv_adjoint_grad(qv_state *s, const qv_gate *g, size_t ng, const qv_pau
  * amplitudes come from FP64 sincospi tables; sums are FP64. Synchronises. */
 qv_status qv_verify_qft(qv_state *s, uint64_t j, double *dist);
 
+/* ||psi_a - psi_b||_2 in FP64 for two states of the same n (either dtype;
+ * e.g. a complex64 run against its complex128 rerun). Runs on a's stream
+ * after synchronising b's. Synchronises. */
+qv_status qv_distance(qv_state *a, qv_state *b, double *out);
+
 /* Allocation-free Z sums (the paper has no counterpart; this exists for
  * callers that cannot allocate device memory). Some callers cannot call
  * cudaMalloc at the point where they need a result: code recording a CUDA

@@ -453,6 +453,15 @@ qv_status qv_verify_qft(qv_state *s, uint64_t j, double *dist)
     return verify_qft(s, j, dist);
 }
 
+qv_status qv_distance(qv_state *a, qv_state *b, double *out)
+{
+    CHECK_HANDLE(a);
+    CHECK_HANDLE(b);
+    if (!out) return fail(QV_ERR_ARG, "out is NULL");
+    if (a->n != b->n) return fail(QV_ERR_ARG, "states differ in n");
+    return distance(a, b, out);
+}
+
 const char *qv_last_error(void) { return g_err; }
 
 }  // extern "C"

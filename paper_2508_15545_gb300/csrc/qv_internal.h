@@ -130,6 +130,7 @@ void adjoint_release(qv_state *s);
 
 // ---------------------------------------------------------------- verification (verify.cu)
 qv_status verify_qft(qv_state *s, uint64_t j, double *dist);
+qv_status distance(qv_state *a, qv_state *b, double *out);
 
 // ---------------------------------------------------------------- reductions (reduce_kernels.cu)
 // out[0] = sum |a|^2, out[1 + q] = sum over bit q set of |a|^2, q < n.

@@ -66,7 +66,56 @@ __global__ void sum_kernel(const double *part, int np, double *out)
     }
 }
 
+template <typename A, typename B>
+__global__ void __launch_bounds__(kThreads) dist_kernel(const A *__restrict__ a, const B *__restrict__ b, uint64_t N,
+                                                        double *part)
+{
+    double acc = 0;
+    for (uint64_t k = uint64_t(blockIdx.x) * kThreads + threadIdx.x; k < N; k += uint64_t(gridDim.x) * kThreads) {
+        const double dr = double(a[2 * k]) - double(b[2 * k]), di = double(a[2 * k + 1]) - double(b[2 * k + 1]);
+        acc += dr * dr + di * di;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ double ws[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0;
+        for (int w = 0; w < kThreads / 32; ++w) s += ws[w];
+        part[blockIdx.x] = s;
+    }
+}
+
 }  // namespace
+
+qv_status distance(qv_state *a, qv_state *b, double *out)
+{
+    QV_CUDA(cudaStreamSynchronize(b->stream));
+    const unsigned grid = unsigned(a->num_sms) * 8;
+    QV_TRY(ensure_scratch(a, (grid + 1) * sizeof(double)));
+    double *part = static_cast<double *>(a->scratch.ptr), *res = part + grid;
+    prof_bytes(a, QV_K_VERIFY, double(dim(a)) * (amp_bytes(a->dt) + amp_bytes(b->dt)));
+    const uint64_t N = dim(a);
+    if (a->dt == QV_C64 && b->dt == QV_C64)
+        QV_LAUNCH(a, QV_K_VERIFY, dist_kernel<float, float><<<grid, kThreads, 0, a->stream>>>(
+                                      static_cast<const float *>(a->amp), static_cast<const float *>(b->amp), N, part));
+    else if (a->dt == QV_C64)
+        QV_LAUNCH(a, QV_K_VERIFY, dist_kernel<float, double><<<grid, kThreads, 0, a->stream>>>(
+                                      static_cast<const float *>(a->amp), static_cast<const double *>(b->amp), N, part));
+    else if (b->dt == QV_C64)
+        QV_LAUNCH(a, QV_K_VERIFY, dist_kernel<double, float><<<grid, kThreads, 0, a->stream>>>(
+                                      static_cast<const double *>(a->amp), static_cast<const float *>(b->amp), N, part));
+    else
+        QV_LAUNCH(a, QV_K_VERIFY, dist_kernel<double, double><<<grid, kThreads, 0, a->stream>>>(
+                                      static_cast<const double *>(a->amp), static_cast<const double *>(b->amp), N, part));
+    QV_LAUNCH(a, QV_K_VERIFY, sum_kernel<<<1, 32, 0, a->stream>>>(part, int(grid), res));
+    QV_TRY(ensure_host_out(a, 1));
+    QV_TRY(copy_d2h(a, a->host_out, res, sizeof(double)));
+    QV_CUDA(cudaStreamSynchronize(a->stream));
+    *out = std::sqrt(std::max(0.0, a->host_out[0]));
+    return QV_OK;
+}
 
 qv_status verify_qft(qv_state *s, uint64_t j, double *dist)
 {

@@ -101,6 +101,7 @@ def _load():
         "qv_batch_run": [ctypes.c_void_p, P],
         "qv_batch_destroy": [ctypes.c_void_p],
         "qv_verify_qft": [_H, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)],
+        "qv_distance": [_H, _H, ctypes.POINTER(ctypes.c_double)],
         "qv_profile": [_H, ctypes.c_int],
         "qv_profile_read": [_H, ctypes.POINTER(qv_kernel_stat), ctypes.c_int],
         "qv_transfer_bytes": [_H, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
@@ -369,6 +370,13 @@ def qv_verify_qft(h: int, j: int) -> float:
     """||psi - QFT|j>||_2 from the closed form, computed on the GPU."""
     d = ctypes.c_double()
     _check(lib.qv_verify_qft(h, j, ctypes.byref(d)))
+    return d.value
+
+
+def qv_distance(a: int, b: int) -> float:
+    """||psi_a - psi_b||_2 (FP64), any mix of dtypes."""
+    d = ctypes.c_double()
+    _check(lib.qv_distance(a, b, ctypes.byref(d)))
     return d.value
 
 

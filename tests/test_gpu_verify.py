@@ -80,3 +80,20 @@ def test_uneven_batch_64_circuits(qvlib, orc, cuda):
     b.close()
     for h in states:
         qv.qv_destroy(h)
+
+
+def test_distance_mixed_precision(qvlib, orc, cuda):
+    qv = qvlib
+    n = 14
+    g = W.random_circuit(n, 5, seed=8)
+    a = qv.qv_create(n, 0)
+    b = qv.qv_create(n, 1)
+    qv.qv_apply_circuit(a, g)
+    qv.qv_apply_circuit(b, g)
+    pa, pb = qv.qv_get_state(a).astype(complex), qv.qv_get_state(b)
+    assert qv.qv_distance(a, b) == pytest.approx(float(np.linalg.norm(pa - pb)), rel=1e-6, abs=1e-12)
+    assert qv.qv_distance(b, b) == 0.0
+    qv.qv_set_basis(b, 1)
+    assert qv.qv_distance(a, b) == pytest.approx(float(np.linalg.norm(pa - np.eye(1 << n)[1])), rel=1e-9)
+    qv.qv_destroy(a)
+    qv.qv_destroy(b)
