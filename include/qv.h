@@ -324,6 +324,12 @@ qv_status qv_batch_run(qv_batch *b, double *expvals);
 
 qv_status qv_batch_destroy(qv_batch *b);
 
+/* Waits for the handle's stream and reports device-side failures: kernels
+ * whose waits are bounded (the compiled fused passes' tile copies, the batch
+ * dependencies) write a status word instead of hanging; this call (and every
+ * call that synchronises) returns QV_ERR_TIMEOUT once when it is set. */
+qv_status qv_sync(qv_state *s);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *qv_last_error(void);
 

@@ -298,7 +298,7 @@ qv_status adjoint_impl(qv_state *s, const qv_gate *g, size_t ng, const qv_pauli_
     const size_t bytes = dim(s) * amp_bytes(s->dt);
     if (B.lam_bytes < bytes) {
         if (B.lam) {
-            QV_CUDA(cudaStreamSynchronize(s->stream));
+            QV_TRY(sync_and_check(s));
             QV_CUDA(cudaFree(B.lam));
             B.lam = nullptr;
             B.lam_bytes = 0;
@@ -323,7 +323,7 @@ qv_status adjoint_impl(qv_state *s, const qv_gate *g, size_t ng, const qv_pauli_
     const size_t need = (slots.size() + 1) * size_t(grid) + slots.size() + 1;
     if (B.part_count < need) {
         if (B.part) {
-            QV_CUDA(cudaStreamSynchronize(s->stream));
+            QV_TRY(sync_and_check(s));
             QV_CUDA(cudaFree(B.part));
             B.part = nullptr;
         }
@@ -397,7 +397,7 @@ qv_status adjoint_impl(qv_state *s, const qv_gate *g, size_t ng, const qv_pauli_
     QV_LAUNCH(s, QV_K_ADJOINT, rows_sum_kernel<<<rows, kThreads, 0, s->stream>>>(part, int(grid), sums));
     QV_TRY(ensure_host_out(s, rows));
     QV_TRY(copy_d2h(s, s->host_out, sums, sizeof(double) * rows));
-    QV_CUDA(cudaStreamSynchronize(s->stream));
+    QV_TRY(sync_and_check(s));
     std::vector<Neumaier> acc(nparams);
     for (size_t k = 0; k < slots.size(); ++k) acc[g[slots[k].gate].param[slots[k].angle]].add(s->host_out[k]);
     if (grad_out)

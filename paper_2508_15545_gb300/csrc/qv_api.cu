@@ -51,6 +51,27 @@ qv_status ensure_scratch(qv_state *s, size_t bytes)
     return QV_OK;
 }
 
+qv_status status_word(qv_state *s, int **out)
+{
+    if (!s->dev_status) {
+        QV_CUDA(cudaMalloc(&s->dev_status, 256));
+        QV_CUDA(cudaMemsetAsync(s->dev_status, 0, 256, s->stream));
+    }
+    *out = s->dev_status;
+    return QV_OK;
+}
+
+qv_status sync_and_check(qv_state *s)
+{
+    QV_CUDA(cudaStreamSynchronize(s->stream));
+    if (!s->dev_status) return QV_OK;
+    int v = 0;
+    QV_CUDA(cudaMemcpy(&v, s->dev_status, sizeof v, cudaMemcpyDeviceToHost));
+    if (v == 0) return QV_OK;
+    QV_CUDA(cudaMemset(s->dev_status, 0, sizeof v));
+    return fail(qv_status(v), "a bounded device-side wait gave up (status %d); the state is unspecified", v);
+}
+
 qv_status ensure_host_out(qv_state *s, size_t count)
 {
     if (s->host_out_len >= count) return QV_OK;
@@ -206,6 +227,7 @@ qv_status qv_destroy(qv_state *s)
     if (s->scratch.ptr) cudaFree(s->scratch.ptr);
     if (s->host_out) cudaFreeHost(s->host_out);
     if (s->owned && s->amp) cudaFree(s->amp);
+    if (s->dev_status) cudaFree(s->dev_status);
     delete s;
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     return QV_OK;
@@ -240,8 +262,7 @@ qv_status qv_get_state(qv_state *s, void *host, size_t bytes)
     if (!host) return fail(QV_ERR_ARG, "host is NULL");
     if (bytes != dim(s) * amp_bytes(s->dt)) return fail(QV_ERR_ARG, "bytes != state size");
     QV_CUDA(cudaMemcpyAsync(host, s->amp, bytes, cudaMemcpyDeviceToHost, s->stream));
-    QV_CUDA(cudaStreamSynchronize(s->stream));
-    return QV_OK;
+    return sync_and_check(s);
 }
 
 qv_status qv_set_state(qv_state *s, const void *host, size_t bytes)
@@ -460,6 +481,12 @@ qv_status qv_distance(qv_state *a, qv_state *b, double *out)
     if (!out) return fail(QV_ERR_ARG, "out is NULL");
     if (a->n != b->n) return fail(QV_ERR_ARG, "states differ in n");
     return distance(a, b, out);
+}
+
+qv_status qv_sync(qv_state *s)
+{
+    CHECK_HANDLE(s);
+    return sync_and_check(s);
 }
 
 const char *qv_last_error(void) { return g_err; }

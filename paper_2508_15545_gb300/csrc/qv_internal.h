@@ -54,6 +54,7 @@ struct qv_state {
     qv::Prof prof;
     qv::PlanCache *plan = nullptr;
     qv::AdjointBuffers *adj = nullptr;
+    int *dev_status = nullptr;    // device status word written by kernels with bounded waits
 };
 
 namespace qv {
@@ -100,6 +101,11 @@ inline size_t amp_bytes(qv_dtype dt) { return dt == QV_C64 ? 8 : 16; }
 inline uint64_t dim(const qv_state *s) { return uint64_t(1) << s->n; }
 
 qv_status ensure_scratch(qv_state *s, size_t bytes);
+// Device status word of the handle (allocated and cleared on first use).
+qv_status status_word(qv_state *s, int **out);
+// Synchronises the handle's stream and reports a nonzero status word
+// (QV_ERR_TIMEOUT from a bounded device wait), clearing it.
+qv_status sync_and_check(qv_state *s);
 qv_status ensure_host_out(qv_state *s, size_t count);
 
 // ---------------------------------------------------------------- gates (host)

@@ -216,7 +216,7 @@ template <typename R> qv_status zsums_impl(qv_state *s, double *out_host)
         QV_LAUNCH(s, QV_K_REDUCE, zsum_combine_kernel<<<n + 1, kThreads, 0, s->stream>>>(part, nblk, out));
         QV_TRY(copy_d2h(s, s->host_out, out, sizeof(double) * (n + 1)));
     }
-    QV_CUDA(cudaStreamSynchronize(s->stream));
+    QV_TRY(sync_and_check(s));
     std::copy(s->host_out, s->host_out + n + 1, out_host);
     return QV_OK;
 }
@@ -267,7 +267,7 @@ template <typename R> qv_status pauli_impl(qv_state *s, const qv_pauli_term *ter
         QV_LAUNCH(s, QV_K_PAULI, sum_parts_kernel<<<1, 32, 0, s->stream>>>(part + k * grid, int(grid), res + k));
     }
     QV_TRY(copy_d2h(s, s->host_out, res, sizeof(double) * ng));
-    QV_CUDA(cudaStreamSynchronize(s->stream));
+    QV_TRY(sync_and_check(s));
     Neumaier tot;
     for (size_t k = 0; k < ng; ++k) tot.add(s->host_out[k]);
     *out_host = tot.value();

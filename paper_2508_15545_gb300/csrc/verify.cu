@@ -112,7 +112,7 @@ qv_status distance(qv_state *a, qv_state *b, double *out)
     QV_LAUNCH(a, QV_K_VERIFY, sum_kernel<<<1, 32, 0, a->stream>>>(part, int(grid), res));
     QV_TRY(ensure_host_out(a, 1));
     QV_TRY(copy_d2h(a, a->host_out, res, sizeof(double)));
-    QV_CUDA(cudaStreamSynchronize(a->stream));
+    QV_TRY(sync_and_check(a));
     *out = std::sqrt(std::max(0.0, a->host_out[0]));
     return QV_OK;
 }
@@ -140,7 +140,7 @@ qv_status verify_qft(qv_state *s, uint64_t j, double *dist)
     QV_LAUNCH(s, QV_K_VERIFY, sum_kernel<<<1, 32, 0, s->stream>>>(part, int(grid), res));
     QV_TRY(ensure_host_out(s, 1));
     QV_TRY(copy_d2h(s, s->host_out, res, sizeof(double)));
-    QV_CUDA(cudaStreamSynchronize(s->stream));
+    QV_TRY(sync_and_check(s));
     *dist = std::sqrt(std::max(0.0, s->host_out[0]));
     return QV_OK;
 }

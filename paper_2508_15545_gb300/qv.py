@@ -101,6 +101,7 @@ def _load():
         "qv_batch_run": [ctypes.c_void_p, P],
         "qv_batch_destroy": [ctypes.c_void_p],
         "qv_verify_qft": [_H, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)],
+        "qv_sync": [_H],
         "qv_distance": [_H, _H, ctypes.POINTER(ctypes.c_double)],
         "qv_profile": [_H, ctypes.c_int],
         "qv_profile_read": [_H, ctypes.POINTER(qv_kernel_stat), ctypes.c_int],
@@ -371,6 +372,10 @@ def qv_verify_qft(h: int, j: int) -> float:
     d = ctypes.c_double()
     _check(lib.qv_verify_qft(h, j, ctypes.byref(d)))
     return d.value
+
+
+def qv_sync(h: int):
+    _check(lib.qv_sync(h))
 
 
 def qv_distance(a: int, b: int) -> float:
