@@ -130,13 +130,28 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def source_hash() -> str:
+# Sources that define each kernel class's device code: a committed ncu figure
+# stays valid while these files are unchanged.
+KERNEL_SOURCES = {
+    "fused": ("fused_jit.cu", "planner.cpp", "planner.h"),
+    "plain": ("pair_kernels.cu", "qv_device.cuh"),
+}
+
+
+def fp32_peak_tflops(sm_count: int, sm_max_mhz) -> float:
+    """FP32 arithmetic peak: 128 FP32 lanes per SM, one FMA (2 operations) per
+    lane and clock, at the maximum SM clock (2070 MHz on GB300 when the
+    sampler saw none)."""
+    mhz = float(sm_max_mhz) if sm_max_mhz else 2070.0
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def source_hash(kernel_class: str) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2508_15545_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, fn), "rb") as f:
-                h.update(fn.encode() + f.read())
+    for fn in KERNEL_SOURCES.get(kernel_class, ()):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode() + f.read())
     return h.hexdigest()[:16]
 
 
@@ -148,10 +163,10 @@ def ncu_traffic(kernel_class: str, mode: str):
         return None
     with open(p) as f:
         d = json.load(f)
-    e = d.get("%s/%s" % (kernel_class, mode))
-    if not e or e.get("source_hash") != source_hash():
+    e = d.get(kernel_class)
+    if not e or e.get("source_hash") != source_hash(kernel_class):
         return None
-    return e.get("dram_bytes_per_launch")
+    return e.get("dram_bytes_per_launch_scaled")
 
 
 # ----------------------------------------------------------------------------
@@ -230,9 +245,11 @@ def run_ours(args):
     cfg["parallelism"] = "replicas%d" % world if world > 1 else "single GPU"
     garr = qv.gates_to_c(gates)
     ng = len(gates)
+    plan_cost = None
     if mode == qv.QV_MODE_FUSED:
         cfg["plan"] = qv.qv_plan_info(args.n, qv.QV_C64, (garr, ng), args.tile_bits)
         cfg["tile_bits"] = args.tile_bits or min(args.n, 12)
+        plan_cost = qv.qv_plan_cost(args.n, qv.QV_C64, (garr, ng), args.tile_bits)
     N = 1 << args.n
 
     stream = torch.cuda.current_stream(dev)
@@ -304,18 +321,37 @@ def run_ours(args):
     dname, (dl, dms, dbytes) = dom
     achieved = dbytes / (dms / 1e3) / 1e9 if dms > 0 else None
     per_launch = dbytes / dl if dl else None
+    roof = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
+            "traffic": ncu_traffic(dname, args.mode),
+            "algorithmic_bytes_per_launch": per_launch,
+            "avg_launch_ms": dms / dl if dl else None,
+            "share_of_step": dms / sum(v[1] for v in tstats.values())}
+    if dname == "fused" and plan_cost and dms > 0:
+        # A fused pass does many gates per HBM round trip: it is bound by FP32
+        # arithmetic when operations / FP32 peak exceed bytes / HBM peak.
+        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+        fp32_peak = fp32_peak_tflops(sm_count, clocks.get("sm_max_mhz"))
+        steps_timed = 2
+        flops_s = plan_cost["flops"] * steps_timed / (dms / 1e3)
+        t_alu = plan_cost["flops"] / (fp32_peak * 1e12)
+        t_hbm = plan_cost["bytes"] / (peak * 1e9)
+        roof["hbm_frac"] = roof["frac"]
+        roof["hbm_achieved_GBps"] = achieved
+        roof["alu"] = {"achieved": flops_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                       "frac": flops_s / 1e12 / fp32_peak, "peak_kind": "derived: SMs x 128 FP32 lanes x 2 x max SM clock",
+                       "flops_per_launch": plan_cost["flops"] / max(1, cfg["plan"]["passes"])}
+        roof["floor_ms_per_step"] = {"hbm": t_hbm * 1e3, "alu": t_alu * 1e3}
+        if t_alu > t_hbm:
+            roof.update({"bound": "alu", "achieved": flops_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": flops_s / 1e12 / fp32_peak, "peak_kind": roof["alu"]["peak_kind"]})
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
         "gpu_launches": launches,
         "clocks": clocks,
-        "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
-                     "traffic": ncu_traffic(dname, args.mode),
-                     "algorithmic_bytes_per_launch": per_launch,
-                     "avg_launch_ms": dms / dl if dl else None,
-                     "share_of_step": dms / sum(v[1] for v in tstats.values())},
+        "roofline": roof,
         "kernel_classes": {k: {"launches": v[0] / 2, "ms": v[1] / 2, "GBps": (v[2] / (v[1] / 1e3) / 1e9) if v[1] else None}
                            for k, v in tstats.items() if v[0]},
     }

@@ -165,6 +165,16 @@ qv_status qv_apply_circuit(qv_state *s, const qv_gate *g, size_t ng, const qv_pl
  * operations. Host only. */
 qv_status qv_plan_info(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t out[4]);
 
+/* Algorithmic cost of the fused plan of g[0..ng) (host only, as qv_plan_info):
+ * out[0] = HBM bytes, one read and one write of the state per pass;
+ * out[1] = floating-point operations: per amplitude and on-chip operation,
+ * 14 for a 2x2 complex matrix (Eq. 5: 4 complex products and 2 sums per
+ * pair), 6 for a diagonal one, 0 for X, half of that when the operation is
+ * controlled (only the amplitudes with the control set change). The
+ * roofline of a fused pass is the larger of bytes / HBM bandwidth and
+ * operations / arithmetic peak. */
+qv_status qv_plan_cost(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, double out[2]);
+
 /* Autotuner: runs g[0..ng) in fused mode with every supported tile size
  * (2^10 .. 2^12 amplitudes, at most 2^n), times each with CUDA events after a
  * warm-up run, and remembers the fastest for this (n, dtype, engine) -- later

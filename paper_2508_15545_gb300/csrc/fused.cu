@@ -173,7 +173,8 @@ qv_status to_pgates(const qv_gate *g, size_t ng, std::vector<plan::PGate> &out)
     return QV_OK;
 }
 
-qv_status plan_info(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t out[4])
+qv_status plan_info(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t out[4],
+                    double cost[2])
 {
     int K = (opts && opts->tile_bits) ? opts->tile_bits : std::min(n, plan::kMaxK);
     if (K < plan::kMinK || K > plan::kMaxK || K > n) return fail(QV_ERR_ARG, "tile_bits %d unsupported for n = %d", K, n);
@@ -185,10 +186,17 @@ qv_status plan_info(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_pl
     const bool fuse = !(opts && (opts->flags & QV_PLAN_NO_FUSION));
     if (!plan::make_plan(n, K, dt == QV_C64, fuse, pg, passes, st, err))
         return fail(QV_ERR_UNSUPPORTED, "planner: %s", err.c_str());
-    out[0] = st.passes;
-    out[1] = st.stages;
-    out[2] = st.transposes;
-    out[3] = st.ops;
+    if (out) {
+        out[0] = st.passes;
+        out[1] = st.stages;
+        out[2] = st.transposes;
+        out[3] = st.ops;
+    }
+    if (cost) {
+        const double N = std::ldexp(1.0, n);
+        cost[0] = 2.0 * st.passes * N * double(amp_bytes(dt));
+        cost[1] = st.flops_per_amp * N;
+    }
     return QV_OK;
 }
 

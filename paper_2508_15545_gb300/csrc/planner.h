@@ -86,6 +86,11 @@ struct Pass {
 
 struct PlanStats {
     int passes = 0, stages = 0, transposes = 0, gates = 0, ops = 0;
+    // algorithmic floating-point operations per amplitude of the state, summed
+    // over all ops: a 2x2 complex matrix on a pair is 28 real operations (14 per
+    // amplitude), a diagonal one 6 per amplitude, X none; a controlled op
+    // (identity when its select bit is 0) updates half the amplitudes
+    double flops_per_amp = 0;
 };
 
 // Plans gates[0..ng) for an n-qubit state with tiles of 2^k amplitudes

@@ -330,7 +330,17 @@ qv_status qv_plan_info(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv
     if (dt != QV_C64 && dt != QV_C128) return fail(QV_ERR_ARG, "bad dtype %d", int(dt));
     if (ng && !g) return fail(QV_ERR_ARG, "gate list is NULL");
     for (size_t k = 0; k < ng; ++k) QV_TRY(validate_gate(g[k], n, k));
-    return plan_info(n, dt, g, ng, opts, out);
+    return plan_info(n, dt, g, ng, opts, out, nullptr);
+}
+
+qv_status qv_plan_cost(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, double out[2])
+{
+    if (!out) return fail(QV_ERR_ARG, "out is NULL");
+    if (n < 1 || n > 40) return fail(QV_ERR_ARG, "n = %d outside [1, 40]", n);
+    if (dt != QV_C64 && dt != QV_C128) return fail(QV_ERR_ARG, "bad dtype %d", int(dt));
+    if (ng && !g) return fail(QV_ERR_ARG, "gate list is NULL");
+    for (size_t k = 0; k < ng; ++k) QV_TRY(validate_gate(g[k], n, k));
+    return plan_info(n, dt, g, ng, opts, nullptr, out);
 }
 
 qv_status qv_permute_qubits(qv_state *s, const int32_t *perm)

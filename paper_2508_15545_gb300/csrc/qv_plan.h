@@ -13,7 +13,10 @@ namespace qv {
 // True when qv_apply_circuit in QV_MODE_AUTO should take the fused path.
 bool fused_supported(const qv_state *s, const qv_plan_opts *opts);
 qv_status apply_fused(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_opts *opts);
-qv_status plan_info(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t out[4]);
+// Plan statistics (out, may be NULL) and algorithmic cost (cost, may be NULL:
+// cost[0] = HBM bytes, cost[1] = floating-point operations) of the fused plan.
+qv_status plan_info(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t out[4],
+                    double cost[2]);
 
 // Bit q of every index moves to bit perm[q].
 qv_status apply_permutation(qv_state *s, const int32_t *perm);

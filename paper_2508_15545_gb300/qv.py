@@ -87,6 +87,8 @@ def _load():
         "qv_permute_qubits": [_H, ctypes.POINTER(ctypes.c_int32)],
         "qv_plan_info": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(qv_gate), ctypes.c_size_t,
                          ctypes.POINTER(qv_plan_opts), ctypes.POINTER(ctypes.c_int32)],
+        "qv_plan_cost": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(qv_gate), ctypes.c_size_t,
+                         ctypes.POINTER(qv_plan_opts), ctypes.POINTER(ctypes.c_double)],
         "qv_norm2": [_H, ctypes.POINTER(ctypes.c_double)],
         "qv_expect_z": [_H, P, P, ctypes.POINTER(ctypes.c_double)],
         "qv_expect_pauli": [_H, ctypes.POINTER(qv_pauli_term), ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)],
@@ -256,6 +258,18 @@ def qv_plan_info(n: int, dtype: int, gates, tile_bits: int = 0, flags: int = 0) 
     opts = plan_opts(QV_MODE_FUSED, tile_bits, flags)
     _check(lib.qv_plan_info(n, dtype, arr, ng, ctypes.byref(opts), out))
     return {"passes": out[0], "stages": out[1], "transposes": out[2], "ops": out[3]}
+
+
+def qv_plan_cost(n: int, dtype: int, gates, tile_bits: int = 0, flags: int = 0) -> dict:
+    """Algorithmic cost of the fused plan (host only): HBM bytes and floating-point operations."""
+    if isinstance(gates, tuple) and len(gates) == 2 and isinstance(gates[1], int):
+        arr, ng = gates
+    else:
+        arr, ng = gates_to_c(gates), len(gates)
+    out = (ctypes.c_double * 2)()
+    opts = plan_opts(QV_MODE_FUSED, tile_bits, flags)
+    _check(lib.qv_plan_cost(n, dtype, arr, ng, ctypes.byref(opts), out))
+    return {"bytes": out[0], "flops": out[1]}
 
 
 def qv_permute_qubits(h: int, perm: Sequence[int]):

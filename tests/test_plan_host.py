@@ -1,0 +1,78 @@
+"""Host-side checks of the fused-pass planner (no GPU): pass counts and the
+algorithmic cost model (HBM bytes, floating-point operations) that the
+roofline of a fused pass is measured against."""
+import math
+
+import pytest
+
+from paper_2508_15545_gb300.workloads import Gate, random_circuit, config_seed, layer_count_gates
+
+
+@pytest.fixture(scope="module")
+def qv(qvlib):
+    return qvlib
+
+
+def cost(qv, n, gates, dtype=0, **kw):
+    return qv.qv_plan_cost(n, dtype, gates, **kw)
+
+
+@pytest.mark.parametrize("dtype,ab", [(0, 8), (1, 16)])
+def test_single_gate_cost(qv, dtype, ab):
+    n, N = 12, 1 << 12
+    u3 = Gate("u3", 0, theta=(0.3, 0.2, 0.1))
+    c = cost(qv, n, [u3], dtype, tile_bits=10)
+    assert c["bytes"] == 2 * N * ab          # one read + one write of the state
+    assert c["flops"] == 14 * N              # Eq. 5: 28 real operations per pair
+    info = qv.qv_plan_info(n, dtype, [u3], tile_bits=10)
+    assert info["passes"] == 1 and info["ops"] == 1
+
+
+def test_op_kinds_cost(qv):
+    n, N = 12, 1 << 12
+    assert cost(qv, n, [Gate("x", 3, ctrl=0)], tile_bits=10)["flops"] == 0          # CNOT: a permutation
+    assert cost(qv, n, [Gate("z", 3, ctrl=0)], tile_bits=10)["flops"] == 3 * N      # CZ: diagonal, half the amps
+    assert cost(qv, n, [Gate("rz", 5, theta=(0.7, 0, 0))], tile_bits=10)["flops"] == 6 * N
+    assert cost(qv, n, [Gate("u3", 4, ctrl=1, theta=(0.3, 0.2, 0.1))], tile_bits=10)["flops"] == 7 * N
+
+
+def test_fusion_reduces_flops(qv):
+    n, N = 12, 1 << 12
+    gates = [Gate("h", 2), Gate("ry", 2, theta=(0.4, 0, 0)), Gate("h", 2)]
+    fused = cost(qv, n, gates, tile_bits=10)
+    unfused = cost(qv, n, gates, tile_bits=10, flags=qv.QV_PLAN_NO_FUSION)
+    assert fused["flops"] == 14 * N
+    assert unfused["flops"] == 3 * 14 * N
+    assert fused["bytes"] == unfused["bytes"] == 2 * N * 8
+
+
+def test_high_qubits_join_the_tile(qv):
+    # gates on qubits far above the contiguous low run still share one pass
+    n = 20
+    gates = [Gate("h", q) for q in (19, 15, 11, 0)]
+    info = qv.qv_plan_info(n, 0, gates, tile_bits=10)
+    assert info["passes"] == 1
+
+
+@pytest.mark.parametrize("k", [10, 11, 12])
+def test_random_circuit_30q_cost_consistent(qv, k):
+    n, layers = 30, 40
+    gates = random_circuit(n, layers, config_seed(1))
+    assert len(gates) == layer_count_gates(n, layers) == 1780
+    info = qv.qv_plan_info(n, 0, gates, tile_bits=k)
+    c = cost(qv, n, gates, tile_bits=k)
+    N = 1 << n
+    assert c["bytes"] == 2 * info["passes"] * N * 8
+    # 1200 U3 (14 per amplitude) at most; fusion only removes work
+    assert 0 < c["flops"] <= 1200 * 14 * N
+    # every pass holds at least one gate; the tiles leave at most n - k qubits out
+    assert 1 <= info["passes"] <= len(gates)
+    assert info["ops"] <= len(gates)
+    assert math.isfinite(c["flops"])
+
+
+def test_plan_cost_rejects_bad_args(qv):
+    with pytest.raises(qv.QvError):
+        qv.qv_plan_cost(0, 0, [Gate("h", 0)])
+    with pytest.raises(qv.QvError):
+        qv.qv_plan_cost(12, 0, [Gate("h", 12)], tile_bits=10)
