@@ -226,6 +226,22 @@ def run_reference(args):
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
+def max_over_ranks(values, device):
+    """Max of each value over all ranks: one all-reduce of the timings, the
+    only collective of a replica run (no data moves between ranks)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Units all replicas processed, divided by the slowest rank's time."""
+    return world * units_per_rank / seconds_max
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -308,13 +324,10 @@ def run_ours(args):
         h2d, d2h = qv.qv_transfer_bytes(h)
         e2e = {"value_s": e2e_s, "h2d": h2d / args.steps, "d2h": d2h / args.steps}
 
-    t = torch.tensor([ms, e2e["value_s"] if e2e else 0.0], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max, e2e_max = float(t[0]), float(t[1])
+    ms_max, e2e_max = max_over_ranks([ms, e2e["value_s"] if e2e else 0.0], dev)
 
     updates = ng * N
-    value = world * updates / (ms_max / 1e3)
+    value = whole_job_rate(updates, world, ms_max / 1e3)
     peak, peak_kind = peaks()
     # dominant kernel class by device time
     dom = max(tstats.items(), key=lambda kv: kv[1][1])
@@ -356,7 +369,7 @@ def run_ours(args):
                            for k, v in tstats.items() if v[0]},
     }
     if e2e:
-        out["e2e"] = {"value": world * updates / e2e_max, "unit": UNIT,
+        out["e2e"] = {"value": whole_job_rate(updates, world, e2e_max), "unit": UNIT,
                       "h2d_bytes_per_step": int(e2e["h2d"]), "d2h_bytes_per_step": int(e2e["d2h"])}
     if not args.no_extras:
         out["extras"] = extras(args, qv, torch, dev, st.h, gates)

@@ -340,6 +340,13 @@ qv_status qv_batch_destroy(qv_batch *b);
  * call that synchronises) returns QV_ERR_TIMEOUT once when it is set. */
 qv_status qv_sync(qv_state *s);
 
+/* Self-test of the bounded device wait (the one the batch kernel uses for
+ * its pass dependencies): one thread waits on a zeroed counter that nothing
+ * increments and gives up after `limit` polls (128 ns apart; limit <= 2^24).
+ * Returns QV_ERR_TIMEOUT on a healthy device, with the handle and its stream
+ * still usable; QV_ERR_ARG for a larger limit. */
+qv_status qv_wait_selftest(qv_state *s, uint32_t limit);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *qv_last_error(void);
 

@@ -37,13 +37,6 @@ struct BItem {
     uint32_t chunk;
 };
 
-__device__ __forceinline__ uint32_t ld_acquire(const unsigned *p)
-{
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 template <typename R, int K>
 __global__ void __launch_bounds__(1 << (K - kRegBits), 1)
     batch_kernel(R *const *amps, const unsigned char *__restrict__ blobs, const BPass *__restrict__ passes,
@@ -73,18 +66,9 @@ __global__ void __launch_bounds__(1 << (K - kRegBits), 1)
         if (item >= nitems) break;
         const BItem it = items[item];
         const BPass P = passes[it.gpass];
-        if (tid == 0 && P.dep >= 0) {
-            const uint32_t need = passes[P.dep].nchunks;
-            uint32_t spins = 0;
-            while (ld_acquire(&done[P.dep]) < need) {
-                if (++spins > spin_limit || *reinterpret_cast<volatile int *>(status) != 0) {
-                    atomicCAS(status, 0, int(QV_ERR_TIMEOUT));
-                    s_abort = 1;
-                    break;
-                }
-                __nanosleep(128);
-            }
-        }
+        if (tid == 0 && P.dep >= 0 &&
+            !wait_counter(&done[P.dep], passes[P.dep].nchunks, spin_limit, status, int(QV_ERR_TIMEOUT)))
+            s_abort = 1;
         __syncthreads();
         if (s_abort) break;
         if (s_cached != int32_t(it.gpass)) {
@@ -207,7 +191,26 @@ __global__ void batch_combine_kernel(const double *part, int count, double *out)
     out[c] = a.value();
 }
 
+// Waits on a counter that nothing increments: runs the timeout path of the
+// bounded wait the batch kernel uses, with no fault and no hang.
+__global__ void wait_selftest_kernel(const unsigned *ctr, uint32_t limit, int *status)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) wait_counter(ctr, 1u, limit, status, int(QV_ERR_TIMEOUT));
+}
+
 }  // namespace
+
+qv_status wait_selftest(qv_state *s, uint32_t limit)
+{
+    if (limit > kSpinLimit) return fail(QV_ERR_ARG, "limit %u above %u", limit, kSpinLimit);
+    int *status = nullptr;
+    QV_TRY(status_word(s, &status));
+    QV_TRY(ensure_scratch(s, 256));
+    unsigned *ctr = static_cast<unsigned *>(s->scratch.ptr);
+    QV_CUDA(cudaMemsetAsync(ctr, 0, sizeof(unsigned), s->stream));
+    QV_LAUNCH(s, QV_K_BATCH, wait_selftest_kernel<<<1, 32, 0, s->stream>>>(ctr, limit, status));
+    return sync_and_check(s);
+}
 
 // ---------------------------------------------------------------- host side
 struct BatchGroup {

@@ -493,6 +493,12 @@ qv_status qv_distance(qv_state *a, qv_state *b, double *out)
     return distance(a, b, out);
 }
 
+qv_status qv_wait_selftest(qv_state *s, uint32_t limit)
+{
+    CHECK_HANDLE(s);
+    return wait_selftest(s, limit);
+}
+
 qv_status qv_sync(qv_state *s)
 {
     CHECK_HANDLE(s);

@@ -6,6 +6,31 @@
 
 namespace qv {
 
+// Load with acquire semantics at GPU scope (pairs with a release increment).
+__device__ __forceinline__ uint32_t ld_acquire_u32(const unsigned *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Bounded wait: polls *ctr until it reaches `need`. Gives up after `limit`
+// polls (128 ns apart) or as soon as another wait has set *status; a wait
+// that gives up sets *status to `code` (if still 0) and returns false.
+__device__ __forceinline__ bool wait_counter(const unsigned *ctr, unsigned need, uint32_t limit, int *status,
+                                             int code)
+{
+    uint32_t spins = 0;
+    while (ld_acquire_u32(ctr) < need) {
+        if (++spins > limit || *reinterpret_cast<volatile int *>(status) != 0) {
+            atomicCAS(status, 0, code);
+            return false;
+        }
+        __nanosleep(128);
+    }
+    return true;
+}
+
 // Insert a 0 at bit position b of x (bits >= b move up by one).
 __host__ __device__ __forceinline__ uint64_t insert_zero(uint64_t x, int b)
 {

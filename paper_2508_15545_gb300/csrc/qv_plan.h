@@ -35,6 +35,8 @@ qv_status autotune(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_opts 
 qv_status batch_create(const qv_batch_item *items, size_t count, const qv_pauli_term *H, size_t nt,
                        const qv_plan_opts *opts, qv_batch **out);
 qv_status batch_run(qv_batch *b, double *expvals);
+// Launches one bounded wait on a counter nothing increments (`limit` polls).
+qv_status wait_selftest(qv_state *s, uint32_t limit);
 void batch_release(qv_batch *b);
 
 }  // namespace qv

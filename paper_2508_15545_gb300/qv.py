@@ -104,6 +104,7 @@ def _load():
         "qv_batch_destroy": [ctypes.c_void_p],
         "qv_verify_qft": [_H, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)],
         "qv_sync": [_H],
+        "qv_wait_selftest": [_H, ctypes.c_uint32],
         "qv_distance": [_H, _H, ctypes.POINTER(ctypes.c_double)],
         "qv_profile": [_H, ctypes.c_int],
         "qv_profile_read": [_H, ctypes.POINTER(qv_kernel_stat), ctypes.c_int],
@@ -390,6 +391,11 @@ def qv_verify_qft(h: int, j: int) -> float:
 
 def qv_sync(h: int):
     _check(lib.qv_sync(h))
+
+
+def qv_wait_selftest(h: int, limit: int):
+    """Runs the bounded device wait into its timeout; raises QvError (QV_ERR_TIMEOUT)."""
+    _check(lib.qv_wait_selftest(h, limit))
 
 
 def qv_distance(a: int, b: int) -> float:

@@ -72,3 +72,25 @@ def test_autotune_picks_a_tile_and_keeps_results_exact(qvlib, orc, cuda):
     qv.qv_apply_circuit(h, g, mode=qv.QV_MODE_FUSED)           # tile_bits = 0: tuned value
     assert np.linalg.norm(qv.qv_get_state(h).astype(complex) - orc.run(n, g)) <= 1e-5
     qv.qv_destroy(h)
+
+
+def test_bounded_wait_reports_timeout(qvlib, orc, cuda):
+    """The batch kernel's dependency wait, run into its limit on a counter
+    nothing increments, reports QV_ERR_TIMEOUT through the status word; the
+    handle, its stream and later kernels keep working."""
+    qv = qvlib
+    n = 12
+    h = qv.qv_create(n, 0)
+    for limit in (0, 1000):
+        with pytest.raises(qv.QvError) as e:
+            qv.qv_wait_selftest(h, limit)
+        assert e.value.status == qv.QV_ERR_TIMEOUT
+        qv.qv_sync(h)   # reported once, then cleared
+    with pytest.raises(qv.QvError) as e:
+        qv.qv_wait_selftest(h, (1 << 24) + 1)
+    assert e.value.status == qv.QV_ERR_ARG
+    gates = W.random_circuit(n, 6, W.config_seed(0, 7))
+    qv.qv_apply_circuit(h, gates)
+    psi = qv.qv_get_state(h)
+    assert np.linalg.norm(psi.astype(complex) - orc.run(n, gates)) <= 1e-5
+    qv.qv_destroy(h)
