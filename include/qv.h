@@ -86,6 +86,9 @@ typedef enum {
 #define QV_PLAN_INTERPRET 2  /* fused mode: run the planner's program with the precompiled
                                 interpreting kernel instead of compiling each pass (NVRTC);
                                 also used when NVRTC cannot be loaded */
+#define QV_PLAN_NO_PAIRS 4   /* fused mode: no 4x4 operations on two register qubits (the
+                                compiled complex64 kernel merges runs of operations on two
+                                qubits into one 4x4 when that takes fewer FP32 operations) */
 
 typedef struct {
     int32_t mode;        /* qv_mode */

@@ -314,7 +314,7 @@ qv_status build(qv_batch *b, const qv_batch_item *items, size_t count, const qv_
         QV_TRY(to_pgates(items[c].gates, items[c].ngates, pg));
         plan::PlanStats st;
         std::string err;
-        if (!plan::make_plan(n, K, b->dt == QV_C64, fuse, pg, plans[c], st, err))
+        if (!plan::make_plan(n, K, b->dt == QV_C64, fuse, false, pg, plans[c], st, err))
             return fail(QV_ERR_UNSUPPORTED, "batch item %zu: planner: %s", c, err.c_str());
         by_k[K].push_back(int(c));
     }

@@ -1,7 +1,8 @@
 // Host-side packing of an on-chip op's coefficients (shared by the
 // interpreted and the compiled fused kernels).
 //
-// complex64: two sets (select = 0 / 1) of 12 f32x2 pairs each: (re, re),
+// complex64: a GEN2 (4x4) op has one set of 16 (re, re), (im, im), (-im, -im)
+// triples, row-major. Other ops: two sets (select = 0 / 1) of 12 f32x2 pairs each: (re, re),
 // (im, im), (-im, -im) for U00, U01, U10, U11 of a general op, or for d0 and
 // d1 of a diagonal op. Where the two packed lanes (tile qubit 0 = 0 / 1) need
 // different values -- a select or a diagonal target on register bit 3 -- the
@@ -35,8 +36,17 @@ inline void lane_triple(uint64_t *dst, std::complex<double> z0, std::complex<dou
     dst[2] = pack_f32x2(float(-z0.imag()), float(-z1.imag()));
 }
 
-inline void op_coeffs_c64(const plan::Op &op, uint64_t out[24])
+// Coefficient slots (u64) an op takes in the compiled complex64 kernel: two
+// sets of 12 for a 2x2 op, 48 for a GEN2 (16 entries, one set).
+inline int coef_slots_c64(const plan::Op &op) { return op.type == plan::OP_GEN2 ? 48 : 24; }
+
+// Writes coef_slots_c64(op) values.
+inline void op_coeffs_c64(const plan::Op &op, uint64_t *out)
 {
+    if (op.type == plan::OP_GEN2) {
+        for (int e = 0; e < 16; ++e) lane_triple(out + 3 * e, op.M4[e], op.M4[e]);
+        return;
+    }
     std::memset(out, 0, 24 * sizeof(uint64_t));
     if (op.type == plan::OP_DIAG) {
         if (op.sreg == 3) {  // select on the lane bit: lane 0 = select 0, lane 1 = select 1

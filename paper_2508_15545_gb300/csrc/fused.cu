@@ -111,6 +111,8 @@ template <typename R> qv_status run_plan(qv_state *s, const std::vector<plan::Pa
     std::vector<unsigned char> buf;
     std::vector<size_t> offs, sizes;
     for (const auto &p : passes) {
+        for (const plan::Op &op : p.ops)
+            if (op.type == plan::OP_GEN2) return fail(QV_ERR_UNSUPPORTED, "4x4 operations need the compiled kernel");
         buf.resize((buf.size() + 255) & ~size_t(255), 0);
         offs.push_back(buf.size());
         serialize<R>(p, buf);
@@ -183,8 +185,11 @@ qv_status plan_info(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_pl
     std::vector<plan::Pass> passes;
     plan::PlanStats st;
     std::string err;
-    const bool fuse = !(opts && (opts->flags & QV_PLAN_NO_FUSION));
-    if (!plan::make_plan(n, K, dt == QV_C64, fuse, pg, passes, st, err))
+    const int flags = opts ? opts->flags : 0;
+    const bool fuse = !(flags & QV_PLAN_NO_FUSION);
+    // as the compiled complex64 engine plans it (host only: NVRTC is not consulted)
+    const bool pairs = dt == QV_C64 && !(flags & (QV_PLAN_INTERPRET | QV_PLAN_NO_PAIRS));
+    if (!plan::make_plan(n, K, dt == QV_C64, fuse, pairs, pg, passes, st, err))
         return fail(QV_ERR_UNSUPPORTED, "planner: %s", err.c_str());
     if (out) {
         out[0] = st.passes;
@@ -211,10 +216,14 @@ qv_status apply_fused(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_op
     std::vector<plan::Pass> passes;
     plan::PlanStats st;
     std::string err;
-    const bool fuse = !(opts && (opts->flags & QV_PLAN_NO_FUSION));
-    if (!plan::make_plan(s->n, K, s->dt == QV_C64, fuse, pg, passes, st, err))
+    const int flags = opts ? opts->flags : 0;
+    const bool fuse = !(flags & QV_PLAN_NO_FUSION);
+    const bool jit = !(flags & QV_PLAN_INTERPRET) && jit_available(nullptr);
+    // 4x4 operations exist only in the compiled complex64 kernel
+    const bool pairs = jit && s->dt == QV_C64 && !(flags & QV_PLAN_NO_PAIRS);
+    if (!plan::make_plan(s->n, K, s->dt == QV_C64, fuse, pairs, pg, passes, st, err))
         return fail(QV_ERR_UNSUPPORTED, "planner: %s", err.c_str());
-    if (!(opts && (opts->flags & QV_PLAN_INTERPRET)) && jit_available(nullptr)) return jit_run_plan(s, passes);
+    if (jit) return jit_run_plan(s, passes);
     return s->dt == QV_C64 ? run_plan<float>(s, passes, K) : run_plan<double>(s, passes, K);
 }
 

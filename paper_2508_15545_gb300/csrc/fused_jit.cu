@@ -266,9 +266,45 @@ std::string coef_load(int base, const std::string &sel, int n, bool dbl)
     return o.str();
 }
 
-void emit_op_c64(std::ostream &o, const plan::Op &op, int k)
+// GEN2: (v_0..v_3) <- M4 (v_0..v_3) for the four packed vectors that differ
+// in register bits A = treg, B = treg2, in both groups of the third bit E.
+// Coefficients are read straight from the parameter bank.
+void emit_gen2_c64(std::ostream &o, const plan::Op &op, int O)
 {
-    const int O = 24 * k;
+    const int A = op.treg, B = op.treg2, E = 3 - A - B;
+    auto C = [&](int j) { return "cf.c[" + std::to_string(O + j) + "]"; };
+    for (int g = 0; g < 2; ++g) {
+        int v[4];
+        v[0] = g << E;
+        v[1] = v[0] | (1 << A);
+        v[2] = v[0] | (1 << B);
+        v[3] = v[1] | (1 << B);
+        o << "    {";
+        for (int n = 0; n < 4; ++n) o << " const u64 xr" << n << " = r[" << v[n] << "], xi" << n << " = i[" << v[n] << "];";
+        o << "\n";
+        for (int m = 0; m < 4; ++m) {
+            std::string er = "f2mul(" + C(3 * (4 * m)) + ", xr0)", ei = "f2mul(" + C(3 * (4 * m)) + ", xi0)";
+            er = "f2fma(" + C(3 * (4 * m) + 2) + ", xi0, " + er + ")";
+            ei = "f2fma(" + C(3 * (4 * m) + 1) + ", xr0, " + ei + ")";
+            for (int n = 1; n < 4; ++n) {
+                const int e = 4 * m + n;
+                er = "f2fma(" + C(3 * e + 2) + ", xi" + std::to_string(n) + ", f2fma(" + C(3 * e) + ", xr" +
+                     std::to_string(n) + ", " + er + "))";
+                ei = "f2fma(" + C(3 * e + 1) + ", xr" + std::to_string(n) + ", f2fma(" + C(3 * e) + ", xi" +
+                     std::to_string(n) + ", " + ei + "))";
+            }
+            o << "      r[" << v[m] << "] = " << er << ";\n      i[" << v[m] << "] = " << ei << ";\n";
+        }
+        o << "    }\n";
+    }
+}
+
+void emit_op_c64(std::ostream &o, const plan::Op &op, int O)
+{
+    if (op.type == plan::OP_GEN2) {
+        emit_gen2_c64(o, op, O);
+        return;
+    }
     const bool us = op.sthr || op.sext;
     const std::string sel =
         us ? "(((tid & " + hex32(op.sthr) + ") != 0u) | ((base & " + hex64(op.sext) + ") != 0ull))" : "0";
@@ -351,7 +387,9 @@ std::string gen_source(const plan::Pass &p, bool c64)
     PassGeom G{p.k, p.k - kRegBits, p.k - kChunkBits, &p};
     const int T = 1 << G.nq;
     const int nops = int(p.ops.size());
-    const int ncoef = std::max(1, nops * (c64 ? 24 : 16));
+    std::vector<int> coff(nops + 1, 0);  // coefficient offset of each op
+    for (int k = 0; k < nops; ++k) coff[k + 1] = coff[k] + (c64 ? coef_slots_c64(p.ops[k]) : 16);
+    const int ncoef = std::max(1, coff[nops]);
     const int nreg = c64 ? 3 : 4;  // register bits addressed per vector/slot (c64: bit 3 is the lane)
     const int nvec = 1 << nreg;
     std::ostringstream o;
@@ -443,7 +481,7 @@ std::string gen_source(const plan::Pass &p, bool c64)
             }
         }
         for (int k = st.op_begin; k < st.op_end; ++k) {
-            if (c64) emit_op_c64(o, p.ops[k], k);
+            if (c64) emit_op_c64(o, p.ops[k], coff[k]);
             else emit_op_c128(o, p.ops[k], k);
         }
     }
@@ -588,11 +626,14 @@ qv_status jit_run_plan(qv_state *s, const std::vector<plan::Pass> &passes)
     std::vector<uint64_t> coef;
     for (size_t i = 0; i < passes.size(); ++i) {
         const plan::Pass &p = passes[i];
-        const size_t per = c64 ? 24 : 16;
-        coef.assign(std::max<size_t>(1, p.ops.size() * per), 0);
-        for (size_t k = 0; k < p.ops.size(); ++k) {
-            if (c64) op_coeffs_c64(p.ops[k], coef.data() + k * per);
-            else op_coeffs_c128(p.ops[k], reinterpret_cast<double *>(coef.data() + k * per));
+        size_t total = 0;
+        for (const plan::Op &op : p.ops) total += c64 ? size_t(coef_slots_c64(op)) : 16;
+        coef.assign(std::max<size_t>(1, total), 0);
+        size_t off = 0;
+        for (const plan::Op &op : p.ops) {
+            if (c64) op_coeffs_c64(op, coef.data() + off);
+            else op_coeffs_c128(op, reinterpret_cast<double *>(coef.data() + off));
+            off += c64 ? size_t(coef_slots_c64(op)) : 16;
         }
         const Compiled &c = *fns[i];
         const uint64_t ntiles = dim(s) >> p.k;

@@ -152,7 +152,186 @@ void matmul(const cd A[4], const cd B[4], cd out[4])  // out = A B
     out[0] = r0; out[1] = r1; out[2] = r2; out[3] = r3;
 }
 
+// ---------------------------------------------------------------- pair fusion
+// A 4x4 over up to two register bits q[0], q[1] (index bit j <-> q[j]; nq = 1
+// leaves index bit 1 as an identity slot).
+struct PairBlock {
+    int q[2] = {-1, -1};
+    int nq = 0;
+    cd M[16];
+    std::vector<int> ops;  // indices of the ops it holds, ascending
+};
+
+// dst (over register bits dq) = src (over sq, nsq used slots) acting as the
+// identity on every bit of dq it does not hold.
+void embed4(const cd src[16], const int sq[2], int nsq, const int dq[2], cd dst[16])
+{
+    int slot[2];  // dst slot j -> src slot or -1
+    for (int j = 0; j < 2; ++j) {
+        slot[j] = -1;
+        for (int i = 0; i < nsq; ++i)
+            if (sq[i] == dq[j] && dq[j] >= 0) slot[j] = i;
+    }
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+            int rs = 0, cs = 0;
+            bool eq = true;
+            for (int j = 0; j < 2; ++j) {
+                const int rb = (r >> j) & 1, cb = (c >> j) & 1;
+                if (slot[j] < 0) eq &= rb == cb;
+                else {
+                    rs |= rb << slot[j];
+                    cs |= cb << slot[j];
+                }
+            }
+            // src slots not mapped (the identity slot of a one-bit source) stay 0
+            dst[4 * r + c] = eq ? src[4 * rs + cs] : cd(0.0);
+        }
+}
+
+void mul4(const cd A[16], const cd B[16], cd out[16])  // out = A B
+{
+    cd t[16];
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+            cd a = 0.0;
+            for (int k = 0; k < 4; ++k) a += A[4 * r + k] * B[4 * k + c];
+            t[4 * r + c] = a;
+        }
+    std::copy(t, t + 16, out);
+}
+
+void ident4(cd M[16])
+{
+    for (int e = 0; e < 16; ++e) M[e] = (e % 5 == 0) ? cd(1.0) : cd(0.0);
+}
+
+// 4x4 of a fusable op (target and select on register bits among q) over q.
+void op_matrix4(const Op &op, const int q[2], cd out[16])
+{
+    auto bit = [&](int idx, int reg) {
+        for (int j = 0; j < 2; ++j)
+            if (q[j] == reg) return (idx >> j) & 1;
+        return 0;
+    };
+    int tj = 0;
+    for (int j = 0; j < 2; ++j)
+        if (q[j] == op.treg) tj = j;
+    for (int e = 0; e < 16; ++e) out[e] = 0.0;
+    for (int c = 0; c < 4; ++c) {
+        const int sel = op.sreg >= 0 ? bit(c, op.sreg) : 0;
+        const int xt = (c >> tj) & 1;
+        if (op.type == OP_DIAG) {
+            out[4 * c + c] = op.M[sel][xt ? 3 : 0];
+            continue;
+        }
+        for (int rt = 0; rt < 2; ++rt) {
+            const int r = (c & ~(1 << tj)) | (rt << tj);
+            out[4 * r + c] += op.M[sel][2 * rt + xt];
+        }
+    }
+}
+
+// Merges, inside each stage, runs of ops on at most two register bits into
+// GEN2 ops when the 4x4 takes fewer FP32 operations than the ops it replaces.
+// An op on other bits commutes with a run, so the run is emitted when it
+// closes (a later op touches one of its bits and cannot join it).
+void fuse_pair_blocks(Pass &P, bool pin0, int &pair_ops)
+{
+    std::vector<Op> nops;
+    std::vector<Stage> nst = P.stages;
+    for (Stage &st : nst) {
+        const int b0 = int(nops.size());
+        std::vector<PairBlock> blocks;
+        std::vector<char> open;
+        int owner[kRegBits] = {-1, -1, -1, -1};
+        auto close = [&](int bi) {
+            PairBlock &B = blocks[bi];
+            double c = 0;
+            for (int o : B.ops) c += fma_per_amp_c64(P.ops[o]);
+            if (B.nq == 2 && c > 16.0 + 1e-9) {
+                Op g{};
+                g.type = OP_GEN2;
+                g.treg = int8_t(B.q[0]);
+                g.treg2 = int8_t(B.q[1]);
+                g.sreg = -1;
+                std::copy(B.M, B.M + 16, g.M4);
+                nops.push_back(g);
+                ++pair_ops;
+            } else {
+                for (int o : B.ops) nops.push_back(P.ops[o]);
+            }
+            for (int j = 0; j < B.nq; ++j) owner[B.q[j]] = -1;
+            open[bi] = 0;
+        };
+        for (int k = st.op_begin; k < st.op_end; ++k) {
+            const Op &op = P.ops[k];
+            int R[2], nr = 0;
+            if (op.treg >= 0) R[nr++] = op.treg;
+            if (op.sreg >= 0 && op.sreg != op.treg) R[nr++] = op.sreg;
+            bool fusable = (op.type == OP_GEN || op.type == OP_X || op.type == OP_DIAG) && op.treg >= 0 && !op.sthr &&
+                           !op.sext && !op.tthr && !op.text;
+            for (int i = 0; i < nr; ++i) fusable &= !(pin0 && R[i] == 3);
+            if (!fusable) {
+                for (int i = 0; i < nr; ++i)
+                    if (owner[R[i]] >= 0) close(owner[R[i]]);
+                nops.push_back(op);
+                continue;
+            }
+            std::vector<int> S;
+            for (int i = 0; i < nr; ++i)
+                if (owner[R[i]] >= 0 && std::find(S.begin(), S.end(), owner[R[i]]) == S.end()) S.push_back(owner[R[i]]);
+            std::vector<int> U;
+            for (int bi : S)
+                for (int j = 0; j < blocks[bi].nq; ++j) U.push_back(blocks[bi].q[j]);
+            for (int i = 0; i < nr; ++i)
+                if (std::find(U.begin(), U.end(), R[i]) == U.end()) U.push_back(R[i]);
+            if (U.size() > 2) {
+                for (int bi : S) close(bi);
+                S.clear();
+                U.assign(R, R + nr);
+            }
+            PairBlock NB;
+            NB.nq = int(U.size());
+            for (int j = 0; j < NB.nq; ++j) NB.q[j] = U[j];
+            ident4(NB.M);
+            for (int bi : S) {
+                cd e[16];
+                embed4(blocks[bi].M, blocks[bi].q, blocks[bi].nq, NB.q, e);
+                mul4(e, NB.M, NB.M);
+                NB.ops.insert(NB.ops.end(), blocks[bi].ops.begin(), blocks[bi].ops.end());
+                open[bi] = 0;
+            }
+            std::sort(NB.ops.begin(), NB.ops.end());
+            cd om[16];
+            op_matrix4(op, NB.q, om);
+            mul4(om, NB.M, NB.M);
+            NB.ops.push_back(k);
+            blocks.push_back(NB);
+            open.push_back(1);
+            for (int j = 0; j < NB.nq; ++j) owner[NB.q[j]] = int(blocks.size()) - 1;
+        }
+        for (size_t bi = 0; bi < blocks.size(); ++bi)
+            if (open[bi]) close(int(bi));
+        st.op_begin = b0;
+        st.op_end = int(nops.size());
+    }
+    P.ops = std::move(nops);
+    P.stages = std::move(nst);
+}
+
 }  // namespace
+
+double fma_per_amp_c64(const Op &op)
+{
+    const bool reg_sel = op.sreg >= 0 && op.sreg != 3;
+    switch (op.type) {
+    case OP_X: return 0.0;
+    case OP_DIAG: return reg_sel && op.m0id ? 2.0 : 4.0;
+    case OP_GEN2: return 16.0;
+    default: return reg_sel && op.m0id ? 4.0 : 8.0;
+    }
+}
 
 int classify(const std::complex<double> U[4])
 {
@@ -161,8 +340,8 @@ int classify(const std::complex<double> U[4])
     return G_GEN;
 }
 
-bool make_plan(int n, int k, bool pin0, bool fuse, const std::vector<PGate> &gates, std::vector<Pass> &out,
-               PlanStats &stats, std::string &err)
+bool make_plan(int n, int k, bool pin0, bool fuse, bool pairs, const std::vector<PGate> &gates,
+               std::vector<Pass> &out, PlanStats &stats, std::string &err)
 {
     out.clear();
     stats = PlanStats{};
@@ -193,7 +372,7 @@ bool make_plan(int n, int k, bool pin0, bool fuse, const std::vector<PGate> &gat
                     ex.push_back(g);
                 }
             }
-            return make_plan(n, k, pin0, fuse, ex, out, stats, err);
+            return make_plan(n, k, pin0, fuse, pairs, ex, out, stats, err);
         }
     }
     std::vector<int> rem(gates.size());
@@ -364,7 +543,7 @@ bool make_plan(int n, int k, bool pin0, bool fuse, const std::vector<PGate> &gat
             }
             if (!fused) {
                 Op op{};
-                op.treg = op.sreg = -1;
+                op.treg = op.sreg = op.treg2 = -1;
                 op.type = g.cls == G_DIAG ? OP_DIAG : g.cls == G_X ? OP_X : OP_GEN;
                 if (op.type == OP_DIAG) coord(t, op.treg, op.tthr, op.text);
                 else op.treg = int8_t(ls.reg_of(pos_of[t]));
@@ -466,13 +645,14 @@ bool make_plan(int n, int k, bool pin0, bool fuse, const std::vector<PGate> &gat
         P.ngates = int(pg.size() - left.size());
         P.stages = std::move(stages);
         P.ops = std::move(ops);
+        if (fuse && pairs) fuse_pair_blocks(P, pin0, stats.pair_ops);
         stats.passes++;
         stats.stages += int(P.stages.size());
         stats.transposes += int(P.stages.size()) - 1;
         stats.gates += P.ngates;
         stats.ops += int(P.ops.size());
         for (const Op &op : P.ops) {
-            const double f = op.type == OP_GEN ? 14.0 : op.type == OP_DIAG ? 6.0 : 0.0;
+            const double f = op.type == OP_GEN ? 14.0 : op.type == OP_DIAG ? 6.0 : op.type == OP_GEN2 ? 30.0 : 0.0;
             stats.flops_per_amp += op.m0id ? 0.5 * f : f;
         }
         out.push_back(std::move(P));

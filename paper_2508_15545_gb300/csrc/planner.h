@@ -42,7 +42,7 @@ struct PGate {
     std::complex<double> U[4];
 };
 
-enum OpType : int8_t { OP_GEN = 0, OP_X = 1, OP_DIAG = 2 };
+enum OpType : int8_t { OP_GEN = 0, OP_X = 1, OP_DIAG = 2, OP_GEN2 = 3 };
 
 // One on-chip operation in the coordinates of the layout of its stage. It
 // applies M[s] to the target qubit, where s is the value of one "select" bit
@@ -50,9 +50,13 @@ enum OpType : int8_t { OP_GEN = 0, OP_X = 1, OP_DIAG = 2 };
 // none: s = 0). A controlled gate is M[0] = I, M[1] = U (m0id = 1); the
 // planner multiplies later gates on the same target into an open op (both
 // branches, or only the s = 1 branch for a gate controlled by the select bit).
+// GEN2 is a dense 4x4 on two register bits (treg, treg2) that replaces a run
+// of ops acting only on those two bits: M4 row-major, index bit 0 <-> treg,
+// bit 1 <-> treg2.
 struct Op {
-    int8_t type;      // OpType: GEN (any 2x2), X (the bit flip, unfused), DIAG (diagonal)
-    int8_t treg;      // target register bit (GEN, X; DIAG with a register target), else -1
+    int8_t type;      // OpType: GEN (any 2x2), X (the bit flip, unfused), DIAG (diagonal), GEN2 (4x4)
+    int8_t treg;      // target register bit (GEN, X, GEN2; DIAG with a register target), else -1
+    int8_t treg2;     // GEN2: second register bit, else -1
     int8_t sreg;      // select register bit, else -1
     int8_t m0id;      // M[0] is the identity
     uint32_t sthr;    // select = this thread-index bit (0: none)
@@ -60,6 +64,7 @@ struct Op {
     uint64_t sext;    // select = this physical qubit outside the tile (0: none)
     uint64_t text;    // DIAG: target physical qubit outside the tile (0: none)
     std::complex<double> M[2][4];   // row-major 2x2 for s = 0 / 1 (DIAG: entries [0], [3])
+    std::complex<double> M4[16];    // GEN2 only
 };
 
 struct Layout {
@@ -85,10 +90,11 @@ struct Pass {
 };
 
 struct PlanStats {
-    int passes = 0, stages = 0, transposes = 0, gates = 0, ops = 0;
+    int passes = 0, stages = 0, transposes = 0, gates = 0, ops = 0, pair_ops = 0;
     // algorithmic floating-point operations per amplitude of the state, summed
     // over all ops: a 2x2 complex matrix on a pair is 28 real operations (14 per
-    // amplitude), a diagonal one 6 per amplitude, X none; a controlled op
+    // amplitude), a diagonal one 6 per amplitude, X none, a 4x4 on a group of
+    // four 30 per amplitude (4 complex products, 3 sums); a controlled op
     // (identity when its select bit is 0) updates half the amplitudes
     double flops_per_amp = 0;
 };
@@ -101,9 +107,15 @@ struct PlanStats {
 // (one 16-byte access = the two amplitudes of one packed pair). Without pin0
 // (16-byte amplitudes) lanes of the load/store layout sit on positions 0..4.
 // Returns false with `err` set on failure.
-// `fuse` = false keeps one op per gate.
-bool make_plan(int n, int k, bool pin0, bool fuse, const std::vector<PGate> &gates, std::vector<Pass> &out,
-               PlanStats &stats, std::string &err);
+// `fuse` = false keeps one op per gate. `pairs` (with `fuse`) then merges runs
+// of ops that act only on two register bits (targets and register selects; not
+// the packed lane bit) into GEN2 ops where that takes fewer FP32 operations.
+bool make_plan(int n, int k, bool pin0, bool fuse, bool pairs, const std::vector<PGate> &gates,
+               std::vector<Pass> &out, PlanStats &stats, std::string &err);
+
+// FP32 fused multiply-adds per amplitude the compiled complex64 kernel spends
+// on `op` (the cost model of the pair fusion).
+double fma_per_amp_c64(const Op &op);
 
 // Classifies a 2x2 matrix: G_DIAG if off-diagonal entries are 0, G_X if it is
 // exactly [[0,1],[1,0]], else G_GEN.

@@ -20,6 +20,7 @@ QV_OK, QV_ERR_ARG, QV_ERR_OOM, QV_ERR_CUDA, QV_ERR_TIMEOUT, QV_ERR_UNSUPPORTED =
 QV_MODE_AUTO, QV_MODE_PLAIN, QV_MODE_FUSED = 0, 1, 2
 QV_PLAN_NO_FUSION = 1
 QV_PLAN_INTERPRET = 2
+QV_PLAN_NO_PAIRS = 4
 STATUS_NAMES = {0: "QV_OK", 1: "QV_ERR_ARG", 2: "QV_ERR_OOM", 3: "QV_ERR_CUDA",
                 4: "QV_ERR_TIMEOUT", 5: "QV_ERR_UNSUPPORTED"}
 KIND = {"h": 0, "x": 1, "y": 2, "z": 3, "s": 4, "sdg": 5, "t": 6, "tdg": 7,

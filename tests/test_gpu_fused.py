@@ -30,8 +30,9 @@ def run_gpu(qv, n, dtype, gates, psi=None, mode=2, tile_bits=0, basis=0, flags=0
         qv.qv_destroy(h)
 
 
-# flags: 0 = compiled passes with gate fusion, 1 = no fusion, 2 = interpreting kernel
-@pytest.mark.parametrize("flags", [0, 1, 2])
+# flags: 0 = compiled passes with gate fusion (and 4x4 pair ops for complex64),
+# 1 = no fusion, 2 = interpreting kernel, 4 = fusion without 4x4 pair ops
+@pytest.mark.parametrize("flags", [0, 1, 2, 4])
 @pytest.mark.parametrize("dtype", [0, 1])
 @pytest.mark.parametrize("n,k", [(10, 10), (11, 10), (11, 11), (12, 12), (13, 10), (13, 12), (16, 11), (17, 12)])
 def test_random_gate_kinds_fused(qvlib, orc, cuda, dtype, n, k, flags):
@@ -122,3 +123,38 @@ def test_fused_reports_bad_tile_bits(qvlib, cuda):
     with pytest.raises(qv.QvError):
         qv.qv_apply_circuit(h, [Gate("h", 0)], mode=qv.QV_MODE_FUSED, tile_bits=12)   # > n
     qv.qv_destroy(h)
+
+
+def pair_heavy_circuit(n, pairs, reps, seed):
+    """Dense runs of gates on two qubits (U3 on each, CNOT both ways, CZ, RZ,
+    controlled U3), the shape the 4x4 pair ops absorb, with a few gates on
+    other qubits between the runs."""
+    rng = W.SplitMix64(seed)
+    gates = []
+    for r in range(reps):
+        for a, b in pairs:
+            th = rng.uniform(9) * 2 * math.pi
+            gates += [Gate("u3", a, theta=tuple(th[0:3])), Gate("u3", b, theta=tuple(th[3:6])),
+                      Gate("x", b, ctrl=a), Gate("rz", a, theta=(th[6], 0, 0)), Gate("z", a, ctrl=b),
+                      Gate("u3", b, ctrl=a, theta=tuple(th[6:9])), Gate("x", a, ctrl=b),
+                      Gate("u3", a, theta=tuple(th[1:4])), Gate("h", b)]
+        gates.append(Gate("h", (r * 5) % n))
+    return gates
+
+
+@pytest.mark.parametrize("n,k,pairs", [(12, 10, [(6, 7)]), (14, 12, [(1, 2), (9, 13)]),
+                                       (16, 11, [(5, 15), (3, 4)]), (13, 12, [(0, 1), (7, 12)])])
+def test_pair_ops_fused(qvlib, orc, cuda, n, k, pairs):
+    """4x4 pair ops (complex64 compiled passes) against the oracle and against
+    the same plan without them; the planner must actually form pair ops."""
+    qv = qvlib
+    gates = pair_heavy_circuit(n, pairs, 6, seed=77 + n)
+    with_pairs = qv.qv_plan_cost(n, 0, gates, tile_bits=k)["flops"]
+    without = qv.qv_plan_cost(n, 0, gates, tile_bits=k, flags=qv.QV_PLAN_NO_PAIRS)["flops"]
+    assert with_pairs < without
+    psi = W.random_state(n, 5 * n + k)
+    want = orc.run(n, gates, psi.copy())
+    got = run_gpu(qv, n, 0, gates, psi=psi, tile_bits=k)
+    got_np = run_gpu(qv, n, 0, gates, psi=psi, tile_bits=k, flags=qv.QV_PLAN_NO_PAIRS)
+    assert dist(got, want) <= TOL[0]
+    assert dist(got_np, want) <= TOL[0]
