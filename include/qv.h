@@ -229,6 +229,16 @@ qv_status qv_apply_pauli(qv_state *s, const qv_pauli_term *terms, size_t nt, qv_
 qv_status qv_adjoint_grad(qv_state *s, const qv_gate *g, size_t ng, const qv_pauli_term *H, size_t nt,
                           size_t nparams, double *grad_out, double *expval_out);
 
+/* qv_adjoint_grad with a choice of reverse sweep: QV_MODE_PLAIN runs one
+ * pass over psi and lambda per gate; QV_MODE_FUSED and QV_MODE_AUTO run it in
+ * tiles (n >= 10): a pass loads 2^k-amplitude tiles of both buffers into
+ * shared memory, applies a run of consecutive reverse-order gates whose
+ * targets lie in the tile (the blocking of Sec. III-B/C, Eq. 6-8, applied to
+ * both buffers) and accumulates their derivatives, and stores both tiles
+ * once. The two sweeps give the same result up to rounding order. */
+qv_status qv_adjoint_grad_ex(qv_state *s, const qv_gate *g, size_t ng, const qv_pauli_term *H, size_t nt,
+                             size_t nparams, double *grad_out, double *expval_out, int32_t sweep_mode);
+
 /* Distance of the state to the closed form of the quantum Fourier transform
  * of the basis state |j> (the paper's workloads have no QFT; this checks large
  * runs on the GPU): *dist = sqrt( sum_k |a_k - exp(2 pi i (j k mod 2^n) / 2^n)

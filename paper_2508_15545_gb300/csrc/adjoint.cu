@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <vector>
 
 #include "qv_device.cuh"
@@ -289,9 +290,427 @@ qv_status pauli_apply_impl(qv_state *s, const void *src, void *dst, const qv_pau
     return QV_OK;
 }
 
+// ---------------------------------------------------------------- tiled reverse sweep
+// The reverse sweep in tiles, as the forward pass does it (Sec. III-B/C/E
+// blocking applied to both buffers): a pass loads a tile of 2^K amplitudes of
+// psi and of lambda into shared memory (the 5 lowest qubits plus K - 5 chosen
+// ones), runs a run of consecutive reverse-order gates whose targets lie in
+// the tile (controls and diagonal targets may lie outside, where they are
+// uniform per tile), and stores both tiles once. Each derivative is summed per
+// thread over its pairs of one tile (at most 16 terms, plain sum), per warp
+// with two-sum compensation in the state's precision, per CTA across tiles in
+// shared memory (compensated), then in FP64 across warps and CTAs.
+namespace tiles {
+
+constexpr int kT = 256;          // threads per CTA
+constexpr int kLow = 5;          // contiguous low qubits of every tile
+constexpr int kMaxSlots = 96;    // derivative slots per pass
+constexpr int kMaxKt = 12;
+
+enum : int32_t { AG_PAIR = 0, AG_DIAG = 1, AG_SWAP = 2 };
+
+template <typename R> struct AGate {
+    int32_t kind;       // AG_*
+    int32_t t, t2;      // tile positions: target (PAIR; DIAG, -1 if outside), both qubits (SWAP)
+    int32_t cpos;       // control tile position, -1 if none in the tile
+    uint64_t cext;      // control outside the tile (physical mask), 0 if none
+    uint64_t text;      // AG_DIAG with the target outside the tile (physical mask)
+    int32_t nd, lslot;  // trainable angles, first local slot
+    R ud[8];            // U^dagger, (re, im) row-major
+    R du[3][8];         // dU / d angle
+};
+
+struct AHead {
+    int32_t ngates, nslots, nseg, pad;
+    int32_t s_high[kMaxKt - kLow];
+    int32_t seg_src[kMaxKt + 1], seg_w[kMaxKt + 1], seg_dst[kMaxKt + 1];
+    int32_t gslot[kMaxSlots];  // global slot of each local slot
+};
+
+template <typename R> struct MaxG { static constexpr int v = 160; };
+template <> struct MaxG<double> { static constexpr int v = 96; };
+
+// One pass, passed by value (kernel parameter space, read through the constant bank).
+template <typename R> struct AProg {
+    AHead h;
+    AGate<R> g[MaxG<R>::v];
+};
+static_assert(sizeof(AProg<float>) < 32000 && sizeof(AProg<double>) < 32000, "kernel parameter limit");
+
+template <typename R> struct V2;
+template <> struct V2<float> { using T = float2; };
+template <> struct V2<double> { using T = double2; };
+
+// Compensated warp sum in precision R: (hi, lo) of every lane -> the warp's
+// total, two-sum on the high parts, low parts added (no FP64 per tile: FP64
+// runs at a small fraction of the FP32 rate on this GPU).
+template <typename R> __device__ __forceinline__ void warp_comp_sum(R &hi, R &lo)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const R h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        R sum, err;
+        two_sum(hi, h2, sum, err);
+        hi = sum;
+        lo += l2 + err;
+    }
+}
+
+template <typename R> __device__ __forceinline__ Mat2<R> mat_of(const R (&m)[8])
+{
+    Mat2<R> u;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        u.r[e] = m[2 * e];
+        u.i[e] = m[2 * e + 1];
+    }
+    return u;
+}
+
+// x with a 0 inserted at bit b (32-bit tile indices)
+__device__ __forceinline__ int ins0(int x, int b) { return ((x >> b) << (b + 1)) | (x & ((1 << b) - 1)); }
+
+// One 2x2 gate of the reverse sweep on the tile (pairs along tile position
+// A.t; with CTRL only pairs whose control bit is 1): psi <- Ud psi, then
+// g[d] += 2 Re <lambda | dU_d psi> over this thread's pairs, lambda <- Ud lambda.
+template <typename R, int NT, int ND, bool CTRL>
+__device__ __forceinline__ void tile_pair(typename V2<R>::T *sp, typename V2<R>::T *sl, const AGate<R> &A,
+                                          R (&g)[3], int tid)
+{
+    using V = typename V2<R>::T;
+    const Mat2<R> ud = mat_of<R>(A.ud);
+    Mat2<R> dm[ND > 0 ? ND : 1];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) dm[d] = mat_of<R>(A.du[d]);
+    const int tq = A.t;
+    const int lo = CTRL ? min(tq, A.cpos) : tq, hi = CTRL ? max(tq, A.cpos) : 0;
+    const int cset = CTRL ? (1 << A.cpos) : 0;
+    constexpr int NP = CTRL ? NT / 4 : NT / 2;
+#pragma unroll
+    for (int j0 = 0; j0 < NP; j0 += kT) {
+        const int j = j0 + tid;
+        int i0 = ins0(j, lo);
+        if (CTRL) i0 = ins0(i0, hi) | cset;
+        const int i1 = i0 | (1 << tq);
+        V a0 = sp[i0], a1 = sp[i1], l0 = sl[i0], l1 = sl[i1];
+        apply2(ud, a0.x, a0.y, a1.x, a1.y);
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            R xr = a0.x, xi = a0.y, yr = a1.x, yi = a1.y;
+            apply2(dm[d], xr, xi, yr, yi);
+            g[d] += R(2) * (l0.x * xr + l0.y * xi + l1.x * yr + l1.y * yi);
+        }
+        apply2(ud, l0.x, l0.y, l1.x, l1.y);
+        sp[i0] = a0;
+        sp[i1] = a1;
+        sl[i0] = l0;
+        sl[i1] = l1;
+    }
+}
+
+// A diagonal gate: one complex factor per amplitude, chosen by the target bit
+// (tile position A.t, or `up` for a target outside the tile).
+template <typename R, int NT, int ND>
+__device__ __forceinline__ void tile_diag(typename V2<R>::T *sp, typename V2<R>::T *sl, const AGate<R> &A, bool up,
+                                          R (&g)[3], int tid)
+{
+    using V = typename V2<R>::T;
+    const R u0r = A.ud[0], u0i = A.ud[1], u3r = A.ud[6], u3i = A.ud[7];
+    R d0r[ND > 0 ? ND : 1], d0i[ND > 0 ? ND : 1], d3r[ND > 0 ? ND : 1], d3i[ND > 0 ? ND : 1];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        d0r[d] = A.du[d][0];
+        d0i[d] = A.du[d][1];
+        d3r[d] = A.du[d][6];
+        d3i[d] = A.du[d][7];
+    }
+    const int t = A.t, c = A.cpos;
+#pragma unroll
+    for (int l0 = 0; l0 < NT; l0 += kT) {
+        const int l = l0 + tid;
+        if (c >= 0 && !((l >> c) & 1)) continue;
+        const bool one = t >= 0 ? ((l >> t) & 1) != 0 : up;
+        V x = sp[l], y = sl[l];
+        cmul(one ? u3r : u0r, one ? u3i : u0i, x.x, x.y);
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            R zr = x.x, zi = x.y;
+            cmul(one ? d3r[d] : d0r[d], one ? d3i[d] : d0i[d], zr, zi);
+            g[d] += R(2) * (y.x * zr + y.y * zi);
+        }
+        cmul(one ? u3r : u0r, one ? u3i : u0i, y.x, y.y);
+        sp[l] = x;
+        sl[l] = y;
+    }
+}
+
+template <typename R> constexpr size_t smem_bytes(int K)
+{
+    return 2 * (size_t(1) << K) * sizeof(typename V2<R>::T) + (size_t(1) << (K - kLow)) * 8 +
+           size_t(kMaxSlots) * (kT / 32) * sizeof(CompSum<R>);
+}
+
+// part[gslot * G + blockIdx.x] = this CTA's sum of each derivative of the pass.
+template <typename R, int K>
+__global__ void __launch_bounds__(kT) adj_tile_kernel(R *__restrict__ psi, R *__restrict__ lam, uint64_t ntiles,
+                                                      const __grid_constant__ AProg<R> P, double *part, int G)
+{
+    using V = typename V2<R>::T;
+    constexpr int NT = 1 << K;
+    extern __shared__ __align__(16) unsigned char smem[];
+    V *sp = reinterpret_cast<V *>(smem);
+    V *sl = sp + NT;
+    uint64_t *phys_hi = reinterpret_cast<uint64_t *>(sl + NT);
+    CompSum<R> *acc = reinterpret_cast<CompSum<R> *>(phys_hi + (NT >> kLow));  // [slot][warp]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const AHead &h = P.h;
+    for (int i = tid; i < (NT >> kLow); i += kT) {
+        uint64_t v = 0;
+        for (int j = 0; j < K - kLow; ++j)
+            if ((i >> j) & 1) v |= uint64_t(1) << h.s_high[j];
+        phys_hi[i] = v;
+    }
+    for (int i = tid; i < h.nslots * (kT / 32); i += kT) acc[i] = CompSum<R>();
+    __syncthreads();
+    V *gp = reinterpret_cast<V *>(psi), *gl = reinterpret_cast<V *>(lam);
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        uint64_t base = 0;
+        for (int q = 0; q < h.nseg; ++q)
+            base |= ((t >> h.seg_src[q]) & ((uint64_t(1) << h.seg_w[q]) - 1)) << h.seg_dst[q];
+        for (int l = tid; l < NT; l += kT) {
+            const uint64_t gi = base | uint64_t(l & 31) | phys_hi[l >> kLow];
+            sp[l] = gp[gi];
+            sl[l] = gl[gi];
+        }
+        __syncthreads();
+        for (int a = 0; a < h.ngates; ++a) {
+            const AGate<R> &A = P.g[a];
+            if (A.cext && !(base & A.cext)) continue;  // control outside the tile is 0: uniform skip
+            if (A.kind == AG_SWAP) {
+                const int lo = min(A.t, A.t2), hi = max(A.t, A.t2);
+                for (int u = tid; u < NT / 4; u += kT) {
+                    const int i = int(insert_zero(insert_zero(uint64_t(u), lo), hi));
+                    const int i1 = i | (1 << A.t), i2 = i | (1 << A.t2);
+                    V x = sp[i1];
+                    sp[i1] = sp[i2];
+                    sp[i2] = x;
+                    x = sl[i1];
+                    sl[i1] = sl[i2];
+                    sl[i2] = x;
+                }
+                __syncthreads();
+                continue;
+            }
+            R gs[3] = {R(0), R(0), R(0)};
+            if (A.kind == AG_DIAG) {
+                const bool up = (base & A.text) != 0;  // target bit when the target lies outside
+                switch (A.nd) {
+                case 0: tile_diag<R, NT, 0>(sp, sl, A, up, gs, tid); break;
+                case 1: tile_diag<R, NT, 1>(sp, sl, A, up, gs, tid); break;
+                case 2: tile_diag<R, NT, 2>(sp, sl, A, up, gs, tid); break;
+                default: tile_diag<R, NT, 3>(sp, sl, A, up, gs, tid); break;
+                }
+            } else if (A.cpos >= 0) {
+                switch (A.nd) {
+                case 0: tile_pair<R, NT, 0, true>(sp, sl, A, gs, tid); break;
+                case 1: tile_pair<R, NT, 1, true>(sp, sl, A, gs, tid); break;
+                case 2: tile_pair<R, NT, 2, true>(sp, sl, A, gs, tid); break;
+                default: tile_pair<R, NT, 3, true>(sp, sl, A, gs, tid); break;
+                }
+            } else {
+                switch (A.nd) {
+                case 0: tile_pair<R, NT, 0, false>(sp, sl, A, gs, tid); break;
+                case 1: tile_pair<R, NT, 1, false>(sp, sl, A, gs, tid); break;
+                case 2: tile_pair<R, NT, 2, false>(sp, sl, A, gs, tid); break;
+                default: tile_pair<R, NT, 3, false>(sp, sl, A, gs, tid); break;
+                }
+            }
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (d >= A.nd) break;
+                R hi = gs[d], lo = R(0);
+                warp_comp_sum(hi, lo);
+                if (lane == 0) {
+                    CompSum<R> &c = acc[(A.lslot + d) * (kT / 32) + warp];
+                    c.add(hi);
+                    c.lo += lo;
+                }
+            }
+            __syncthreads();
+        }
+        for (int l = tid; l < NT; l += kT) {
+            const uint64_t gi = base | uint64_t(l & 31) | phys_hi[l >> kLow];
+            gp[gi] = sp[l];
+            gl[gi] = sl[l];
+        }
+        __syncthreads();
+    }
+    for (int sidx = tid; sidx < h.nslots; sidx += kT) {
+        double v = 0;
+        for (int w = 0; w < kT / 32; ++w) v += acc[sidx * (kT / 32) + w].value();
+        part[size_t(h.gslot[sidx]) * G + blockIdx.x] = v;
+    }
+}
+
+}  // namespace tiles
+
+// Reverse sweep in tiled passes. gate_slot[l] = global slot of gate l's first
+// trainable angle. part has G columns per slot and must be zero beforehand
+// (a pass writes only the columns of the CTAs it launches).
+template <typename R>
+qv_status adjoint_sweep_tiled(qv_state *s, const qv_gate *g, size_t ng, const std::vector<int> &gate_slot,
+                              double *part, int G)
+{
+    using namespace tiles;
+    const int n = s->n;
+    const int K = std::min(n, sizeof(R) == 4 ? 12 : 11);
+    const int maxg = MaxG<R>::v;
+    auto kern = K == 12 ? adj_tile_kernel<R, 12> : K == 11 ? adj_tile_kernel<R, 11> : adj_tile_kernel<R, 10>;
+    const size_t smem = smem_bytes<R>(K);
+    QV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    int per_sm = 0;
+    QV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kT, smem));
+    if (per_sm < 1) return fail(QV_ERR_UNSUPPORTED, "tiled reverse sweep does not fit on an SM");
+    const uint64_t ntiles = dim(s) >> K;
+    const unsigned grid = unsigned(std::min<uint64_t>({ntiles, uint64_t(per_sm) * s->num_sms, uint64_t(G)}));
+    R *psi = static_cast<R *>(s->amp), *lam = static_cast<R *>(s->adj->lam);
+
+    // A gate is applied as diagonal (target may lie outside the tile) when its
+    // matrix and every derivative matrix are diagonal: RX(0) is the identity,
+    // but its derivative is not.
+    auto diagonal = [&](const qv_gate &G1) {
+        cd U[4], dU[3][4];
+        int sl[3];
+        gate_matrix(G1, U);
+        bool d = U[1] == 0.0 && U[2] == 0.0;
+        const int nd = gate_derivs(G1, dU, sl);
+        for (int k = 0; k < nd; ++k) d &= dU[k][1] == 0.0 && dU[k][2] == 0.0;
+        return d;
+    };
+    std::vector<size_t> rem;  // gates still to sweep, in reverse order
+    for (size_t l = ng; l-- > 0;) rem.push_back(l);
+    auto prog = std::make_unique<AProg<R>>();
+    while (!rem.empty()) {
+        std::vector<char> inS(n, 0), blocked(n, 0);
+        for (int q = 0; q < kLow; ++q) inS[q] = 1;
+        int room = K - kLow, nslots = 0;
+        std::vector<size_t> taken, left;
+        for (size_t l : rem) {
+            const qv_gate &G1 = g[l];
+            int qs[3], nq = 0;
+            qs[nq++] = G1.target;
+            if (G1.kind == QV_G_SWAP) qs[nq++] = G1.target2;
+            if (G1.ctrl >= 0) qs[nq++] = G1.ctrl;
+            bool blk = false;
+            for (int i = 0; i < nq; ++i) blk |= blocked[qs[i]] != 0;
+            bool ok = !blk && int(taken.size()) < maxg;
+            int need[2], nn = 0;
+            int nd = 0;
+            if (ok) {
+                if (G1.kind == QV_G_SWAP) {
+                    need[nn++] = G1.target;
+                    need[nn++] = G1.target2;
+                } else {
+                    if (!diagonal(G1)) need[nn++] = G1.target;
+                    for (int a = 0; a < 3; ++a) nd += G1.param[a] >= 0;
+                }
+                int add = 0;
+                for (int i = 0; i < nn; ++i) add += !inS[need[i]];
+                ok = add <= room && nslots + nd <= kMaxSlots;
+            }
+            if (ok) {
+                for (int i = 0; i < nn; ++i)
+                    if (!inS[need[i]]) {
+                        inS[need[i]] = 1;
+                        --room;
+                    }
+                nslots += nd;
+                taken.push_back(l);
+            } else {
+                for (int i = 0; i < nq; ++i) blocked[qs[i]] = 1;
+                left.push_back(l);
+            }
+        }
+        if (taken.empty()) return fail(QV_ERR_UNSUPPORTED, "tiled reverse sweep made no progress");
+        for (int q = kLow; q < n && room > 0; ++q)
+            if (!inS[q]) {
+                inS[q] = 1;
+                --room;
+            }
+        AHead &hd = prog->h;
+        std::memset(&hd, 0, sizeof hd);
+        std::vector<int> pos_of(n, -1);
+        for (int q = 0; q < kLow; ++q) pos_of[q] = q;
+        int j = 0;
+        for (int q = kLow; q < n; ++q)
+            if (inS[q]) {
+                hd.s_high[j] = q;
+                pos_of[q] = kLow + j;
+                ++j;
+            }
+        int src = 0;
+        for (int q = 0; q < n;) {
+            if (inS[q]) {
+                ++q;
+                continue;
+            }
+            int w = 0;
+            while (q + w < n && !inS[q + w]) ++w;
+            hd.seg_src[hd.nseg] = src;
+            hd.seg_w[hd.nseg] = w;
+            hd.seg_dst[hd.nseg] = q;
+            hd.nseg++;
+            src += w;
+            q += w;
+        }
+        hd.ngates = int(taken.size());
+        for (size_t a = 0; a < taken.size(); ++a) {
+            const qv_gate &G1 = g[taken[a]];
+            AGate<R> &A = prog->g[a];
+            std::memset(&A, 0, sizeof A);
+            A.cpos = -1;
+            if (G1.ctrl >= 0) {
+                if (pos_of[G1.ctrl] >= 0) A.cpos = pos_of[G1.ctrl];
+                else A.cext = uint64_t(1) << G1.ctrl;
+            }
+            if (G1.kind == QV_G_SWAP) {
+                A.kind = AG_SWAP;
+                A.t = pos_of[G1.target];
+                A.t2 = pos_of[G1.target2];
+                continue;
+            }
+            cd U[4], dU[3][4];
+            gate_matrix(G1, U);
+            const cd Ud[4] = {std::conj(U[0]), std::conj(U[2]), std::conj(U[1]), std::conj(U[3])};
+            for (int e = 0; e < 4; ++e) {
+                A.ud[2 * e] = R(Ud[e].real());
+                A.ud[2 * e + 1] = R(Ud[e].imag());
+            }
+            int sl[3];
+            A.nd = gate_derivs(G1, dU, sl);
+            for (int d = 0; d < A.nd; ++d)
+                for (int e = 0; e < 4; ++e) {
+                    A.du[d][2 * e] = R(dU[d][e].real());
+                    A.du[d][2 * e + 1] = R(dU[d][e].imag());
+                }
+            if (A.nd) {
+                A.lslot = hd.nslots;
+                for (int d = 0; d < A.nd; ++d) hd.gslot[hd.nslots++] = gate_slot[taken[a]] + d;
+            }
+            A.kind = diagonal(G1) ? AG_DIAG : AG_PAIR;
+            A.t = pos_of[G1.target];  // -1 (outside the tile) only for a diagonal gate
+            if (A.t < 0) A.text = uint64_t(1) << G1.target;
+        }
+        prof_bytes(s, QV_K_ADJOINT, 4.0 * double(dim(s)) * amp_bytes(s->dt));
+        QV_LAUNCH(s, QV_K_ADJOINT, kern<<<grid, kT, smem, s->stream>>>(psi, lam, ntiles, *prog, part, G));
+        rem.swap(left);
+    }
+    return QV_OK;
+}
+
 template <typename R>
 qv_status adjoint_impl(qv_state *s, const qv_gate *g, size_t ng, const qv_pauli_term *H, size_t nt, size_t nparams,
-                       double *grad_out, double *expval_out)
+                       double *grad_out, double *expval_out, bool tiled)
 {
     if (!s->adj) s->adj = new AdjointBuffers;
     AdjointBuffers &B = *s->adj;
@@ -349,7 +768,14 @@ qv_status adjoint_impl(qv_state *s, const qv_gate *g, size_t ng, const qv_pauli_
     // 3. reverse sweep
     R *psi = static_cast<R *>(s->amp), *lam = static_cast<R *>(B.lam);
     size_t slot_next = slots.size();
-    for (size_t l = ng; l-- > 0;) {
+    const bool use_tiles = tiled && s->n >= 10;
+    if (use_tiles) {
+        std::vector<int> gate_slot(ng, -1);
+        for (size_t k = slots.size(); k-- > 0;) gate_slot[slots[k].gate] = int(k);
+        if (!slots.empty()) QV_CUDA(cudaMemsetAsync(part, 0, slots.size() * grid * sizeof(double), s->stream));
+        QV_TRY(adjoint_sweep_tiled<R>(s, g, ng, gate_slot, part, int(grid)));
+    }
+    for (size_t l = use_tiles ? 0 : ng; l-- > 0;) {
         const qv_gate &G = g[l];
         if (G.kind == QV_G_SWAP) {
             const uint64_t units = dim(s) >> 2;
@@ -415,10 +841,10 @@ qv_status pauli_apply(qv_state *s, const void *src, void *dst, const qv_pauli_te
 }
 
 qv_status adjoint_grad(qv_state *s, const qv_gate *g, size_t ng, const qv_pauli_term *H, size_t nt, size_t nparams,
-                       double *grad_out, double *expval_out)
+                       double *grad_out, double *expval_out, bool tiled)
 {
-    return s->dt == QV_C64 ? adjoint_impl<float>(s, g, ng, H, nt, nparams, grad_out, expval_out)
-                           : adjoint_impl<double>(s, g, ng, H, nt, nparams, grad_out, expval_out);
+    return s->dt == QV_C64 ? adjoint_impl<float>(s, g, ng, H, nt, nparams, grad_out, expval_out, tiled)
+                           : adjoint_impl<double>(s, g, ng, H, nt, nparams, grad_out, expval_out, tiled);
 }
 
 void adjoint_release(qv_state *s)

@@ -97,6 +97,8 @@ def _load():
         "qv_apply_pauli": [_H, ctypes.POINTER(qv_pauli_term), ctypes.c_size_t, _H],
         "qv_adjoint_grad": [_H, ctypes.POINTER(qv_gate), ctypes.c_size_t, ctypes.POINTER(qv_pauli_term),
                             ctypes.c_size_t, ctypes.c_size_t, P, ctypes.POINTER(ctypes.c_double)],
+        "qv_adjoint_grad_ex": [_H, ctypes.POINTER(qv_gate), ctypes.c_size_t, ctypes.POINTER(qv_pauli_term),
+                            ctypes.c_size_t, ctypes.c_size_t, P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32],
         "qv_autotune": [_H, ctypes.POINTER(qv_gate), ctypes.c_size_t, ctypes.POINTER(qv_plan_opts),
                         ctypes.POINTER(ctypes.c_int32)],
         "qv_batch_create": [ctypes.POINTER(qv_batch_item), ctypes.c_size_t, ctypes.POINTER(qv_pauli_term),
@@ -310,17 +312,18 @@ def qv_apply_pauli(h: int, terms, out_h: int):
     _check(lib.qv_apply_pauli(h, terms_to_c(terms), len(terms), out_h))
 
 
-def qv_adjoint_grad(h: int, gates, terms, nparams: int):
+def qv_adjoint_grad(h: int, gates, terms, nparams: int, sweep_mode: int = QV_MODE_AUTO):
     """Adjoint-method gradient of <H> over the circuit ``gates`` applied to the
-    handle's current state. Returns (grad as numpy array, <H>)."""
+    handle's current state. Returns (grad as numpy array, <H>). ``sweep_mode``:
+    QV_MODE_PLAIN = one pass per gate, QV_MODE_FUSED / AUTO = tiled passes."""
     if isinstance(gates, tuple) and len(gates) == 2 and isinstance(gates[1], int):
         arr, ng = gates
     else:
         arr, ng = gates_to_c(gates), len(gates)
     grad = np.zeros(max(1, nparams))
     e = ctypes.c_double()
-    _check(lib.qv_adjoint_grad(h, arr, ng, terms_to_c(terms), len(terms), nparams, grad.ctypes.data,
-                               ctypes.byref(e)))
+    _check(lib.qv_adjoint_grad_ex(h, arr, ng, terms_to_c(terms), len(terms), nparams, grad.ctypes.data,
+                                  ctypes.byref(e), sweep_mode))
     return grad[:nparams], e.value
 
 

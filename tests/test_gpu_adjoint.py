@@ -31,12 +31,12 @@ def test_apply_pauli_sum(qvlib, orc, cuda, dtype, n):
     qv.qv_destroy(b)
 
 
-def _adjoint(qv, n, dtype, gates, terms, npar, psi0=None):
+def _adjoint(qv, n, dtype, gates, terms, npar, psi0=None, sweep=0):
     h = qv.qv_create(n, dtype)
     if psi0 is not None:
         qv.qv_set_state(h, psi0)
     before = qv.qv_get_state(h)
-    g, e = qv.qv_adjoint_grad(h, gates, terms, npar)
+    g, e = qv.qv_adjoint_grad(h, gates, terms, npar, sweep_mode=sweep)
     after = qv.qv_get_state(h)
     qv.qv_destroy(h)
     return g, e, before, after
@@ -67,15 +67,17 @@ def test_adjoint_mixed_gates(qvlib, orc, cuda, dtype):
     assert np.linalg.norm(after.astype(complex) - before.astype(complex)) <= (1e-5 if dtype == 0 else 1e-12)
 
 
+# sweep: 1 = one pass per gate, 2 = tiled passes
+@pytest.mark.parametrize("sweep", [1, 2])
 @pytest.mark.parametrize("dtype", [0, 1])
-def test_adjoint_ansatz_12q_vs_param_shift_and_fd(qvlib, orc, cuda, dtype):
+def test_adjoint_ansatz_12q_vs_param_shift_and_fd(qvlib, orc, cuda, dtype, sweep):
     """12-qubit copy of the 26-qubit gradient workload: 16 layers of RY, RZ and
     a CZ ring (384 parameters), H = sum Z_i Z_i+1 + 0.5 sum X_i."""
     qv = qvlib
     n, layers = 12, 16
     gates, npar = W.ansatz_circuit(n, layers, W.config_seed(3, 1))
     terms = W.ansatz_hamiltonian(n)
-    g, e, _, _ = _adjoint(qv, n, dtype, gates, terms, npar)
+    g, e, _, _ = _adjoint(qv, n, dtype, gates, terms, npar, sweep=sweep)
     ps = orc.param_shift_grad(n, gates, terms, npar)
     fd = orc.finite_diff_grad(n, gates, terms, npar, h=1e-3)
     l1 = sum(abs(c) for c, _, _ in terms)
@@ -113,3 +115,75 @@ def test_adjoint_rejects_bad_params(qvlib, cuda):
     with pytest.raises(qv.QvError):
         qv.qv_adjoint_grad(h, [Gate("ry", 0, param=(3, -1, -1))], [(1.0, 0, 1)], 2)
     qv.qv_destroy(h)
+
+
+def _mixed_trainable(n, count, seed):
+    """Random trainable gates on every qubit, controls near and far (outside
+    a tile), diagonal gates on qubits outside a tile, SWAPs, fixed gates."""
+    rng = W.SplitMix64(seed)
+    gates, p = [], 0
+    for k in range(count):
+        u = rng.uniform(6)
+        t = int(u[0] * n) % n
+        c = int(u[1] * n) % n
+        kind = ("u3", "rx", "ry", "rz", "p", "h", "swap", "cz", "cx")[int(u[2] * 9) % 9]
+        th = (float(u[3]) * 6.0 - 3.0, float(u[4]) * 6.0 - 3.0, float(u[5]) * 6.0 - 3.0)
+        ctrl = c if (c != t and u[5] < 0.35) else -1
+        if kind == "swap":
+            if c != t:
+                gates.append(Gate("swap", t, target2=c))
+            continue
+        if kind in ("cz", "cx"):
+            if c != t:
+                gates.append(Gate("z" if kind == "cz" else "x", t, ctrl=c))
+            continue
+        if kind == "h":
+            gates.append(Gate("h", t))
+            continue
+        na = 3 if kind == "u3" else 1
+        par = tuple(p + a if a < na else -1 for a in range(3))
+        p += na
+        gates.append(Gate(kind, t, ctrl=ctrl, theta=th if kind == "u3" else (th[0], 0.0, 0.0), param=par))
+    return gates, p
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("n", [13, 15])
+def test_adjoint_tiled_sweep_mixed(qvlib, orc, cuda, dtype, n):
+    """Tiled reverse sweep on states of several tiles: controls and diagonal
+    targets outside the tile, SWAPs, every trainable kind; against the
+    oracle's parameter-shift gradient and against the per-gate sweep."""
+    qv = qvlib
+    gates, npar = _mixed_trainable(n, 70, seed=400 + n)
+    terms = W.ansatz_hamiltonian(n) + [(0.35, 0b1010, 0b0110), (-0.2, 0, (1 << n) - 1)]
+    psi0 = W.random_state(n, 9 + n)
+    g2, e2, before, after = _adjoint(qv, n, dtype, gates, terms, npar, psi0, sweep=2)
+    g1, e1, _, _ = _adjoint(qv, n, dtype, gates, terms, npar, psi0, sweep=1)
+    ref = orc.param_shift_grad(n, gates, terms, npar, psi0)
+    tol = 2e-4 if dtype == 0 else 1e-10
+    assert e2 == pytest.approx(orc.energy(n, gates, terms, psi0), abs=tol)
+    assert np.max(np.abs(g2 - ref)) <= tol
+    assert np.max(np.abs(g2 - g1)) <= tol
+    assert np.linalg.norm(after.astype(complex) - before.astype(complex)) <= (2e-5 if dtype == 0 else 1e-12)
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_adjoint_tiled_zero_angles(qvlib, orc, cuda, dtype):
+    """Trainable gates at angle 0 are diagonal (RX(0) = I, U3(0, p, l) =
+    diag(1, e^{i(p+l)})) while their derivatives are not: the tiled sweep must
+    still bring their targets into the tile."""
+    qv = qvlib
+    n = 14
+    gates = [Gate("h", q) for q in range(n)]
+    gates += [Gate("rx", 13, theta=(0.0, 0, 0), param=(0, -1, -1)),
+              Gate("ry", 12, theta=(0.0, 0, 0), param=(1, -1, -1)),
+              Gate("u3", 11, theta=(0.0, 0.4, -0.9), param=(2, 3, 4)),
+              Gate("x", 13, ctrl=2), Gate("rx", 10, ctrl=13, theta=(0.0, 0, 0), param=(5, -1, -1)),
+              Gate("rz", 9, theta=(0.0, 0, 0), param=(6, -1, -1)),
+              Gate("u3", 13, theta=(0.7, 0.1, 0.2), param=(7, -1, 8))]
+    terms = [(1.0, 1 << 13, 0), (0.5, 1 << 12, 1 << 11), (0.25, 0, (1 << 10) | (1 << 9)), (0.3, 1 << 11, 0)]
+    psi0 = W.random_state(n, 123)
+    g, e, _, _ = _adjoint(qv, n, dtype, gates, terms, 9, psi0, sweep=2)
+    ref = orc.param_shift_grad(n, gates, terms, 9, psi0)
+    tol = 1e-4 if dtype == 0 else 1e-10
+    assert np.max(np.abs(g - ref)) <= tol, (g, ref)
