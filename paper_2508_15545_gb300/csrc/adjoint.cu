@@ -36,39 +36,43 @@ constexpr int kMaxD = 3;  // trainable angles per gate (U3)
 
 // ---------------------------------------------------------------- H|psi>
 constexpr int kMaxTerms = 64;
-struct PauliGroupA {
+// Terms sharing one X mask; coefficients coeff * i^{ny} in the state's
+// precision (the sum over terms is per amplitude, not a reduction over the
+// state, and FP64 runs at a small fraction of the FP32 rate on this GPU).
+template <typename R> struct PauliGroupA {
     uint64_t x;
-    int nt;
+    int64_t nt;
     uint64_t z[kMaxTerms];
-    double cre[kMaxTerms], cim[kMaxTerms];
+    R cre[kMaxTerms], cim[kMaxTerms];
 };
 
 // out_j = sum over groups sum_t c_t i^{ny_t} (-1)^{popcount(src & z_t)} psi_src, src = j ^ x
 template <typename R>
 __global__ void __launch_bounds__(kThreads) pauli_apply_kernel(const R *__restrict__ psi, R *__restrict__ out,
-                                                               uint64_t N, const PauliGroupA *groups, int ng)
+                                                               uint64_t N, const PauliGroupA<R> *groups, int ng)
 {
     extern __shared__ unsigned char smem_raw[];
-    PauliGroupA *g = reinterpret_cast<PauliGroupA *>(smem_raw);
-    for (int k = threadIdx.x; k < ng * int(sizeof(PauliGroupA) / 8); k += kThreads)
+    PauliGroupA<R> *g = reinterpret_cast<PauliGroupA<R> *>(smem_raw);
+    static_assert(sizeof(PauliGroupA<R>) % 8 == 0, "copied as 8-byte words");
+    for (int k = threadIdx.x; k < ng * int(sizeof(PauliGroupA<R>) / 8); k += kThreads)
         reinterpret_cast<uint64_t *>(g)[k] = reinterpret_cast<const uint64_t *>(groups)[k];
     __syncthreads();
     for (uint64_t j = uint64_t(blockIdx.x) * kThreads + threadIdx.x; j < N; j += uint64_t(gridDim.x) * kThreads) {
-        double ar = 0, ai = 0;
+        R ar = 0, ai = 0;
         for (int q = 0; q < ng; ++q) {
             const uint64_t src = j ^ g[q].x;
-            double cr = 0, ci = 0;
-            for (int k = 0; k < g[q].nt; ++k) {
-                const double sg = (__popcll(src & g[q].z[k]) & 1) ? -1.0 : 1.0;
-                cr += sg * g[q].cre[k];
-                ci += sg * g[q].cim[k];
+            R cr = 0, ci = 0;
+            for (int k = 0; k < int(g[q].nt); ++k) {
+                const bool neg = __popcll(src & g[q].z[k]) & 1;
+                cr += neg ? -g[q].cre[k] : g[q].cre[k];
+                ci += neg ? -g[q].cim[k] : g[q].cim[k];
             }
-            const double vr = psi[2 * src], vi = psi[2 * src + 1];
+            const R vr = psi[2 * src], vi = psi[2 * src + 1];
             ar += cr * vr - ci * vi;
             ai += cr * vi + ci * vr;
         }
-        out[2 * j] = R(ar);
-        out[2 * j + 1] = R(ai);
+        out[2 * j] = ar;
+        out[2 * j + 1] = ai;
     }
 }
 
@@ -254,12 +258,12 @@ unsigned grid_of(const qv_state *s, uint64_t work)
 template <typename R>
 qv_status pauli_apply_impl(qv_state *s, const void *src, void *dst, const qv_pauli_term *terms, size_t nt)
 {
-    std::vector<PauliGroupA> groups;
+    std::vector<PauliGroupA<R>> groups;
     for (size_t k = 0; k < nt; ++k) {
         const uint64_t x = terms[k].xmask, z = terms[k].zmask;
         const int ny = __builtin_popcountll(x & z);
         static const double pr[4] = {1, 0, -1, 0}, pi[4] = {0, 1, 0, -1};
-        PauliGroupA *g = nullptr;
+        PauliGroupA<R> *g = nullptr;
         for (auto &gg : groups)
             if (gg.x == x && gg.nt < kMaxTerms) { g = &gg; break; }
         if (!g) {
@@ -269,11 +273,11 @@ qv_status pauli_apply_impl(qv_state *s, const void *src, void *dst, const qv_pau
             g->x = x;
         }
         g->z[g->nt] = z;
-        g->cre[g->nt] = terms[k].coeff * pr[ny & 3];
-        g->cim[g->nt] = terms[k].coeff * pi[ny & 3];
+        g->cre[g->nt] = R(terms[k].coeff * pr[ny & 3]);
+        g->cim[g->nt] = R(terms[k].coeff * pi[ny & 3]);
         g->nt++;
     }
-    const size_t gbytes = groups.size() * sizeof(PauliGroupA);
+    const size_t gbytes = groups.size() * sizeof(PauliGroupA<R>);
     if (gbytes > 200 * 1024) return fail(QV_ERR_UNSUPPORTED, "Hamiltonian too large (%zu X-mask groups)", groups.size());
     QV_TRY(ensure_scratch(s, std::max<size_t>(gbytes, 8)));
     if (!groups.empty()) QV_TRY(copy_h2d(s, s->scratch.ptr, groups.data(), gbytes));
@@ -286,7 +290,7 @@ qv_status pauli_apply_impl(qv_state *s, const void *src, void *dst, const qv_pau
     QV_LAUNCH(s, QV_K_PAULI,
               pauli_apply_kernel<R><<<grid_of(s, dim(s)), kThreads, gbytes, s->stream>>>(
                   static_cast<const R *>(src), static_cast<R *>(dst), dim(s),
-                  static_cast<const PauliGroupA *>(s->scratch.ptr), int(groups.size())));
+                  static_cast<const PauliGroupA<R> *>(s->scratch.ptr), int(groups.size())));
     return QV_OK;
 }
 

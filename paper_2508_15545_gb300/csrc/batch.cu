@@ -135,6 +135,7 @@ struct BGroup {
     int nt;
     uint64_t z[kMaxGroupTerms];
     double cre[kMaxGroupTerms], cim[kMaxGroupTerms];
+    float fre[kMaxGroupTerms], fim[kMaxGroupTerms];  // the same in FP32, for complex64 states
 };
 
 // part[state * kBlocksPerState + block] = sum over this block's share of the
@@ -162,9 +163,17 @@ __global__ void __launch_bounds__(kBThreads) batch_pauli_kernel(R *const *amps, 
             const R pr = br * ar + bi * ai, pi = br * ai - bi * ar;  // conj(b) a
             R cr = 0, ci = 0;
             for (int k = 0; k < g[q].nt; ++k) {
-                const R sg = (__popcll(i & g[q].z[k]) & 1) ? R(-1) : R(1);
-                cr += sg * R(g[q].cre[k]);
-                ci += sg * R(g[q].cim[k]);
+                const bool neg = __popcll(i & g[q].z[k]) & 1;
+                R ur, ui;
+                if constexpr (sizeof(R) == 4) {
+                    ur = g[q].fre[k];
+                    ui = g[q].fim[k];
+                } else {
+                    ur = g[q].cre[k];
+                    ui = g[q].cim[k];
+                }
+                cr += neg ? -ur : ur;
+                ci += neg ? -ui : ui;
             }
             acc.add(pr * cr - pi * ci);
         }
@@ -411,6 +420,8 @@ qv_status build(qv_batch *b, const qv_batch_item *items, size_t count, const qv_
             g->z[g->nt] = z;
             g->cre[g->nt] = H[k].coeff * pr[ny & 3];
             g->cim[g->nt] = H[k].coeff * pi[ny & 3];
+            g->fre[g->nt] = float(g->cre[g->nt]);
+            g->fim[g->nt] = float(g->cim[g->nt]);
             g->nt++;
         }
         if (hg.size() * sizeof(BGroup) > 200 * 1024) return fail(QV_ERR_UNSUPPORTED, "Hamiltonian too large");

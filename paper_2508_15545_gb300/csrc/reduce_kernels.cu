@@ -163,7 +163,13 @@ __global__ void __launch_bounds__(kThreads) pauli_kernel(const R *__restrict__ a
 {
     __shared__ double smem[kThreads / 32][1];
     __shared__ PauliGroup sg;
+    __shared__ R cre[kMaxTermsPerGroup], cim[kMaxTermsPerGroup];  // in the state's precision, converted once
     if (threadIdx.x == 0) sg = *g;
+    __syncthreads();
+    for (int k = threadIdx.x; k < sg.nt; k += kThreads) {
+        cre[k] = R(sg.cre[k]);
+        cim[k] = R(sg.cim[k]);
+    }
     __syncthreads();
     CompSum<R> acc;
     for (uint64_t i = uint64_t(blockIdx.x) * kThreads + threadIdx.x; i < N; i += uint64_t(gridDim.x) * kThreads) {
@@ -174,9 +180,9 @@ __global__ void __launch_bounds__(kThreads) pauli_kernel(const R *__restrict__ a
         const R pr = br * ar + bi * ai, pi = br * ai - bi * ar;
         R cr = 0, ci = 0;
         for (int k = 0; k < sg.nt; ++k) {
-            const R sgn = (__popcll(i & sg.z[k]) & 1) ? R(-1) : R(1);
-            cr += sgn * R(sg.cre[k]);
-            ci += sgn * R(sg.cim[k]);
+            const bool neg = __popcll(i & sg.z[k]) & 1;
+            cr += neg ? -cre[k] : cre[k];
+            ci += neg ? -cim[k] : cim[k];
         }
         acc.add(pr * cr - pi * ci);
     }
