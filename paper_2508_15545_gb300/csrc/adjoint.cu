@@ -311,7 +311,9 @@ constexpr int kLow = 5;          // contiguous low qubits of every tile
 constexpr int kMaxSlots = 96;    // derivative slots per pass
 constexpr int kMaxKt = 12;
 
-enum : int32_t { AG_PAIR = 0, AG_DIAG = 1, AG_SWAP = 2 };
+enum : int32_t { AG_PAIR = 0, AG_DIAG = 1, AG_SWAP = 2, AG_SIGN = 3, AG_PAIR_REAL = 4 };
+// AG_SIGN: diagonal, entries +-1, no trainable angle (Z, CZ); AG_PAIR_REAL: a
+// 2x2 whose matrix and derivatives are real (RY, H, X), no control.
 
 template <typename R> struct AGate {
     int32_t kind;       // AG_*
@@ -412,6 +414,70 @@ __device__ __forceinline__ void tile_pair(typename V2<R>::T *sp, typename V2<R>:
     }
 }
 
+// apply2 for a real matrix (imaginary parts zero): half the multiplications
+template <typename R>
+__device__ __forceinline__ void apply2_real(const Mat2<R> &U, R &ar, R &ai, R &br, R &bi)
+{
+    const R xr = ar, xi = ai, yr = br, yi = bi;
+    ar = U.r[0] * xr + U.r[1] * yr;
+    ai = U.r[0] * xi + U.r[1] * yi;
+    br = U.r[2] * xr + U.r[3] * yr;
+    bi = U.r[2] * xi + U.r[3] * yi;
+}
+
+// tile_pair for a real, uncontrolled gate
+template <typename R, int NT, int ND>
+__device__ __forceinline__ void tile_pair_real(typename V2<R>::T *sp, typename V2<R>::T *sl, const AGate<R> &A,
+                                               R (&g)[3], int tid)
+{
+    using V = typename V2<R>::T;
+    const Mat2<R> ud = mat_of<R>(A.ud);
+    Mat2<R> dm[ND > 0 ? ND : 1];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) dm[d] = mat_of<R>(A.du[d]);
+    const int tq = A.t;
+#pragma unroll
+    for (int j0 = 0; j0 < NT / 2; j0 += kT) {
+        const int i0 = ins0(j0 + tid, tq), i1 = i0 | (1 << tq);
+        V a0 = sp[i0], a1 = sp[i1], l0 = sl[i0], l1 = sl[i1];
+        apply2_real(ud, a0.x, a0.y, a1.x, a1.y);
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            R xr = a0.x, xi = a0.y, yr = a1.x, yi = a1.y;
+            apply2_real(dm[d], xr, xi, yr, yi);
+            g[d] += R(2) * (l0.x * xr + l0.y * xi + l1.x * yr + l1.y * yi);
+        }
+        apply2_real(ud, l0.x, l0.y, l1.x, l1.y);
+        sp[i0] = a0;
+        sp[i1] = a1;
+        sl[i0] = l0;
+        sl[i1] = l1;
+    }
+}
+
+// A diagonal gate with entries +-1 and nothing to differentiate: sign flips.
+template <typename R, int NT>
+__device__ __forceinline__ void tile_sign(typename V2<R>::T *sp, typename V2<R>::T *sl, const AGate<R> &A, bool up,
+                                          int tid)
+{
+    using V = typename V2<R>::T;
+    const R s0 = A.ud[0], s3 = A.ud[6];
+    const int t = A.t, c = A.cpos;
+#pragma unroll
+    for (int l0 = 0; l0 < NT; l0 += kT) {
+        const int l = l0 + tid;
+        if (c >= 0 && !((l >> c) & 1)) continue;
+        const R f = (t >= 0 ? ((l >> t) & 1) != 0 : up) ? s3 : s0;
+        V x = sp[l], y = sl[l];
+        x.x *= f;
+        x.y *= f;
+        y.x *= f;
+        y.y *= f;
+        sp[l] = x;
+        sl[l] = y;
+    }
+}
+
 // A diagonal gate: one complex factor per amplitude, chosen by the target bit
 // (tile position A.t, or `up` for a target outside the tile).
 template <typename R, int NT, int ND>
@@ -506,7 +572,16 @@ __global__ void __launch_bounds__(kT) adj_tile_kernel(R *__restrict__ psi, R *__
                 continue;
             }
             R gs[3] = {R(0), R(0), R(0)};
-            if (A.kind == AG_DIAG) {
+            if (A.kind == AG_SIGN) {
+                tile_sign<R, NT>(sp, sl, A, (base & A.text) != 0, tid);
+            } else if (A.kind == AG_PAIR_REAL) {
+                switch (A.nd) {
+                case 0: tile_pair_real<R, NT, 0>(sp, sl, A, gs, tid); break;
+                case 1: tile_pair_real<R, NT, 1>(sp, sl, A, gs, tid); break;
+                case 2: tile_pair_real<R, NT, 2>(sp, sl, A, gs, tid); break;
+                default: tile_pair_real<R, NT, 3>(sp, sl, A, gs, tid); break;
+                }
+            } else if (A.kind == AG_DIAG) {
                 const bool up = (base & A.text) != 0;  // target bit when the target lies outside
                 switch (A.nd) {
                 case 0: tile_diag<R, NT, 0>(sp, sl, A, up, gs, tid); break;
@@ -702,6 +777,14 @@ qv_status adjoint_sweep_tiled(qv_state *s, const qv_gate *g, size_t ng, const st
                 for (int d = 0; d < A.nd; ++d) hd.gslot[hd.nslots++] = gate_slot[taken[a]] + d;
             }
             A.kind = diagonal(G1) ? AG_DIAG : AG_PAIR;
+            bool real = true;  // matrix and derivatives real
+            for (int e = 0; e < 4; ++e) {
+                real &= U[e].imag() == 0.0;
+                for (int d = 0; d < A.nd; ++d) real &= dU[d][e].imag() == 0.0;
+            }
+            if (A.kind == AG_DIAG && real && A.nd == 0 && std::abs(U[0].real()) == 1.0 && std::abs(U[3].real()) == 1.0)
+                A.kind = AG_SIGN;
+            if (A.kind == AG_PAIR && real && G1.ctrl < 0) A.kind = AG_PAIR_REAL;
             A.t = pos_of[G1.target];  // -1 (outside the tile) only for a diagonal gate
             if (A.t < 0) A.text = uint64_t(1) << G1.target;
         }
