@@ -229,13 +229,22 @@ qv_status qv_apply_pauli(qv_state *s, const qv_pauli_term *terms, size_t nt, qv_
 qv_status qv_adjoint_grad(qv_state *s, const qv_gate *g, size_t ng, const qv_pauli_term *H, size_t nt,
                           size_t nparams, double *grad_out, double *expval_out);
 
-/* qv_adjoint_grad with a choice of reverse sweep: QV_MODE_PLAIN runs one
- * pass over psi and lambda per gate; QV_MODE_FUSED and QV_MODE_AUTO run it in
- * tiles (n >= 10): a pass loads 2^k-amplitude tiles of both buffers into
- * shared memory, applies a run of consecutive reverse-order gates whose
- * targets lie in the tile (the blocking of Sec. III-B/C, Eq. 6-8, applied to
- * both buffers) and accumulates their derivatives, and stores both tiles
- * once. The two sweeps give the same result up to rounding order. */
+/* Reverse sweeps of qv_adjoint_grad_ex. QV_SWEEP_PER_GATE: one pass over psi
+ * and lambda per gate. QV_SWEEP_TILES (n >= 10): a pass loads 2^k-amplitude
+ * tiles of both buffers into shared memory, runs consecutive reverse-order
+ * gates whose targets lie in the tile (the blocking of Sec. III-B/C, Eq. 6-8,
+ * applied to both buffers) and accumulates their derivatives, then stores
+ * both tiles once. QV_SWEEP_COMPILED (complex64, n >= 10, NVRTC present;
+ * otherwise as QV_SWEEP_TILES): the same passes planned and compiled like the
+ * forward passes, both tiles held in registers. QV_SWEEP_AUTO picks the
+ * compiled sweep where it applies, else the tiled one. All give the same
+ * result up to rounding order. */
+#define QV_SWEEP_AUTO 0
+#define QV_SWEEP_PER_GATE 1
+#define QV_SWEEP_TILES 2
+#define QV_SWEEP_COMPILED 3
+
+/* qv_adjoint_grad with a choice of reverse sweep (QV_SWEEP_*). */
 qv_status qv_adjoint_grad_ex(qv_state *s, const qv_gate *g, size_t ng, const qv_pauli_term *H, size_t nt,
                              size_t nparams, double *grad_out, double *expval_out, int32_t sweep_mode);
 

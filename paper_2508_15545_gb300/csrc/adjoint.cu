@@ -16,8 +16,10 @@
 #include <memory>
 #include <vector>
 
+#include "planner.h"
 #include "qv_device.cuh"
 #include "qv_internal.h"
+#include "qv_jit.h"
 #include "qv_plan.h"
 
 namespace qv {
@@ -795,9 +797,52 @@ qv_status adjoint_sweep_tiled(qv_state *s, const qv_gate *g, size_t ng, const st
     return QV_OK;
 }
 
+// Reverse sweep as compiled passes (complex64): the daggered gates in reverse
+// order, planned like a forward circuit; each gate with trainable angles
+// carries its derivative matrices and gets an op of its own.
+qv_status adjoint_sweep_compiled(qv_state *s, const qv_gate *g, size_t ng, const std::vector<int> &gate_slot,
+                                 double *part, int G)
+{
+    std::vector<plan::PGate> pg;
+    pg.reserve(ng);
+    for (size_t l = ng; l-- > 0;) {
+        const qv_gate &G1 = g[l];
+        plan::PGate p{};
+        p.t = G1.target;
+        p.t2 = -1;
+        p.c = G1.ctrl;
+        if (G1.kind == QV_G_SWAP) {
+            p.cls = plan::G_SWAP;
+            p.t2 = G1.target2;
+            pg.push_back(p);
+            continue;
+        }
+        cd U[4], dU[3][4];
+        gate_matrix(G1, U);
+        p.U[0] = std::conj(U[0]);
+        p.U[1] = std::conj(U[2]);
+        p.U[2] = std::conj(U[1]);
+        p.U[3] = std::conj(U[3]);
+        int sl[3];
+        p.nd = gate_derivs(G1, dU, sl);
+        p.slot = p.nd ? gate_slot[l] : -1;
+        for (int d = 0; d < p.nd; ++d)
+            for (int e = 0; e < 4; ++e) p.dU[d][e] = dU[d][e];
+        p.cls = p.nd > 0 ? plan::G_GEN : plan::classify(p.U);
+        pg.push_back(p);
+    }
+    std::vector<plan::Pass> passes;
+    plan::PlanStats st;
+    std::string err;
+    const int K = std::min(s->n, plan::kMaxK);
+    if (!plan::make_plan(s->n, K, true, true, false, pg, passes, st, err))
+        return fail(QV_ERR_UNSUPPORTED, "planner: %s", err.c_str());
+    return jit_run_adjoint(s, passes, s->adj->lam, part, G);
+}
+
 template <typename R>
 qv_status adjoint_impl(qv_state *s, const qv_gate *g, size_t ng, const qv_pauli_term *H, size_t nt, size_t nparams,
-                       double *grad_out, double *expval_out, bool tiled)
+                       double *grad_out, double *expval_out, int sweep)
 {
     if (!s->adj) s->adj = new AdjointBuffers;
     AdjointBuffers &B = *s->adj;
@@ -855,12 +900,14 @@ qv_status adjoint_impl(qv_state *s, const qv_gate *g, size_t ng, const qv_pauli_
     // 3. reverse sweep
     R *psi = static_cast<R *>(s->amp), *lam = static_cast<R *>(B.lam);
     size_t slot_next = slots.size();
-    const bool use_tiles = tiled && s->n >= 10;
+    const bool use_tiles = sweep != QV_SWEEP_PER_GATE && s->n >= 10;
     if (use_tiles) {
         std::vector<int> gate_slot(ng, -1);
         for (size_t k = slots.size(); k-- > 0;) gate_slot[slots[k].gate] = int(k);
         if (!slots.empty()) QV_CUDA(cudaMemsetAsync(part, 0, slots.size() * grid * sizeof(double), s->stream));
-        QV_TRY(adjoint_sweep_tiled<R>(s, g, ng, gate_slot, part, int(grid)));
+        const bool compiled = sweep != QV_SWEEP_TILES && sizeof(R) == 4 && jit_available(nullptr);
+        if (compiled) QV_TRY(adjoint_sweep_compiled(s, g, ng, gate_slot, part, int(grid)));
+        else QV_TRY(adjoint_sweep_tiled<R>(s, g, ng, gate_slot, part, int(grid)));
     }
     for (size_t l = use_tiles ? 0 : ng; l-- > 0;) {
         const qv_gate &G = g[l];
@@ -928,10 +975,10 @@ qv_status pauli_apply(qv_state *s, const void *src, void *dst, const qv_pauli_te
 }
 
 qv_status adjoint_grad(qv_state *s, const qv_gate *g, size_t ng, const qv_pauli_term *H, size_t nt, size_t nparams,
-                       double *grad_out, double *expval_out, bool tiled)
+                       double *grad_out, double *expval_out, int sweep)
 {
-    return s->dt == QV_C64 ? adjoint_impl<float>(s, g, ng, H, nt, nparams, grad_out, expval_out, tiled)
-                           : adjoint_impl<double>(s, g, ng, H, nt, nparams, grad_out, expval_out, tiled);
+    return s->dt == QV_C64 ? adjoint_impl<float>(s, g, ng, H, nt, nparams, grad_out, expval_out, sweep)
+                           : adjoint_impl<double>(s, g, ng, H, nt, nparams, grad_out, expval_out, sweep);
 }
 
 void adjoint_release(qv_state *s)

@@ -178,6 +178,39 @@ template <int J, int C, int S> QI void d_op(u64 (&r)[8], u64 (&i)[8], const u64 
     }
 }
 
+// adjoint: sum over the pairs along register bit J (with select bit C == S when
+// C >= 0) of Re( conj(l) . (D x) ), x the psi pair, l the lambda pair (packed)
+template <int J, int C, int S> QI float gd_reg(const u64 (&r)[8], const u64 (&i)[8], const u64 (&lr)[8],
+                                               const u64 (&li)[8], const u64 (&d)[12]) {
+    u64 acc = 0ull;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        if ((v >> J) & 1) continue;
+        if (C >= 0 && ((v >> C) & 1) != S) continue;
+        const int w = v | (1 << J);
+        u64 xr = r[v], xi = i[v], yr = r[w], yi = i[w];
+        ap2(d, xr, xi, yr, yi);
+        acc = f2fma(lr[v], xr, acc); acc = f2fma(li[v], xi, acc);
+        acc = f2fma(lr[w], yr, acc); acc = f2fma(li[w], yi, acc);
+    }
+    float a0, a1; upk(acc, a0, a1); return a0 + a1;
+}
+// the same for a target on the packed lane (tile qubit 0): scalar pairs
+template <int C, int S> QI float gd_lane(const u64 (&r)[8], const u64 (&i)[8], const u64 (&lr)[8],
+                                         const u64 (&li)[8], const u64 (&d)[12]) {
+    float acc = 0.f;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        if (C >= 0 && ((v >> C) & 1) != S) continue;
+        float a0, a1, b0, b1, p0, p1, q0, q1;
+        upk(r[v], a0, a1); upk(i[v], b0, b1);
+        ap1(d, a0, b0, a1, b1);
+        upk(lr[v], p0, p1); upk(li[v], q0, q1);
+        acc += p0 * a0 + q0 * b0 + p1 * a1 + q1 * b1;
+    }
+    return acc;
+}
+
 // complex128, scalar slots m = 0..15; m8 = re, im of U00 U01 U10 U11
 QI void ap1d(const double (&m)[8], double &ar, double &ai, double &br, double &bi) {
     const double xr = ar, xi = ai, yr = br, yi = bi;
@@ -505,6 +538,204 @@ std::string gen_source(const plan::Pass &p, bool c64)
     return o.str();
 }
 
+// ---------------------------------------------------------------- adjoint passes (complex64)
+// The reverse sweep of the adjoint gradient as compiled passes: psi and lambda
+// tiles both live in registers (same layouts, same transposes), every op of
+// the pass is applied to both, and an op that carries derivatives also sums
+// 2 Re <lambda | D psi> over the thread's pairs between its psi and lambda
+// updates (the planner gives such an op to its gate alone). Per tile, each
+// derivative is summed over a warp (shuffles) and added to a compensated
+// per-CTA accumulator in shared memory; the CTA writes one partial per slot.
+
+std::string for_lambda(const std::string &code)
+{
+    std::string out;
+    size_t pos = 0;
+    for (;;) {
+        const size_t q = code.find("(r, i", pos);
+        if (q == std::string::npos) break;
+        out += code.substr(pos, q - pos) + "(rl, il";
+        pos = q + 5;
+    }
+    return out + code.substr(pos);
+}
+
+int coef_slots_adj(const plan::Op &op) { return 24 + 12 * op.nd; }
+
+void emit_adj_op_c64(std::ostream &o, const plan::Op &op, int O, int lslot)
+{
+    if (op.nd == 0) {
+        std::ostringstream a;
+        emit_op_c64(a, op, O);
+        o << a.str() << for_lambda(a.str());
+        return;
+    }
+    // a gate with derivatives: GEN op, M[0] = I when it is controlled (m0id)
+    const bool us = op.sthr || op.sext;
+    const std::string sel =
+        us ? "(((tid & " + hex32(op.sthr) + ") != 0u) | ((base & " + hex64(op.sext) + ") != 0ull))" : "0";
+    const int J = op.treg, C = op.sreg;
+    std::string apply, grad;
+    int s = 0;
+    if (C < 0) {
+        apply = J < 3 ? "g_all<" + std::to_string(J) + ">(r, i, c);" : "g_lane<-1, 0>(r, i, c);";
+        grad = J < 3 ? "gd_reg<" + std::to_string(J) + ", -1, 0>" : "gd_lane<-1, 0>";
+    } else if (C == 3) {  // select on the packed lane: coefficients resolved per lane
+        apply = "g_all<" + std::to_string(J) + ">(r, i, c);";
+        grad = "gd_reg<" + std::to_string(J) + ", -1, 0>";
+    } else {
+        s = 1;  // controlled by a register bit: only the s = 1 half changes
+        apply = J < 3 ? "g_sel<" + std::to_string(J) + ", " + std::to_string(C) + ", 1>(r, i, c);"
+                      : "g_lane<" + std::to_string(C) + ", 1>(r, i, c);";
+        grad = J < 3 ? "gd_reg<" + std::to_string(J) + ", " + std::to_string(C) + ", 1>"
+                     : "gd_lane<" + std::to_string(C) + ", 1>";
+    }
+    o << "    { float gsum[" << op.nd << "] = {";
+    for (int d = 0; d < op.nd; ++d) o << (d ? ", " : "") << "0.f";
+    o << "};\n";
+    o << "      const int s = " << sel << ";\n";
+    // a runtime select (control on a thread bit or outside the tile) skips the op where it is 0;
+    // register selects are resolved inside the op
+    const std::string cond = C < 0 ? std::string("s || ") + (op.m0id ? "0" : "1") : std::string("1");
+    o << "      if (" << cond << ") { " << coef_load(O, C < 0 ? "s" : std::to_string(s), 12, false)
+      << "\n        " << apply << "\n";
+    for (int d = 0; d < op.nd; ++d) {
+        o << "        { u64 dc[12];";
+        for (int e = 0; e < 12; ++e) o << " dc[" << e << "] = cf.c[" << O + 24 + 12 * d + e << "];";
+        o << " gsum[" << d << "] = " << grad << "(r, i, rl, il, dc); }\n";
+    }
+    o << "        " << for_lambda(apply) << "\n      }\n";
+    for (int d = 0; d < op.nd; ++d)
+        o << "      acc_add(sacc, " << lslot + d << ", warp, lane, gsum[" << d << "]);\n";
+    o << "    }\n";
+}
+
+std::string gen_source_adj(const plan::Pass &p, int nslots)
+{
+    PassGeom G{p.k, p.k - kRegBits, p.k - kChunkBits, &p};
+    const int T = 1 << G.nq;
+    const int nops = int(p.ops.size());
+    std::vector<int> coff(nops + 1, 0), lsl(nops, 0);
+    int ls = 0;
+    for (int k = 0; k < nops; ++k) {
+        coff[k + 1] = coff[k] + coef_slots_adj(p.ops[k]);
+        lsl[k] = ls;
+        ls += p.ops[k].nd;
+    }
+    const int ncoef = std::max(1, coff[nops]);
+    std::ostringstream o;
+    o << kPrelude;
+    o << "struct QvAdjArgs { u64 c[" << ncoef << "]; int gslot[" << std::max(1, nslots) << "]; };\n";
+    o << "#define NW " << T / 32 << "\n";
+    o << "QI void acc_add(float *sacc, int q, int warp, int lane, float v) {\n"
+         "#pragma unroll\n"
+         "    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);\n"
+         "    if (lane == 0) { float *h = sacc + 2 * (q * NW + warp); const float t = h[0] + v;\n"
+         "        const float bb = t - h[0]; h[1] += (h[0] - (t - bb)) + (v - bb); h[0] = t; }\n"
+         "}\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(" << T << ", " << (p.k == 12 ? 2 : p.k == 11 ? 4 : 8)
+      << ") qv_adj(float *__restrict__ amp, float *__restrict__ lam, u64 ntiles, double *part, int Gc, "
+         "const QvAdjArgs cf)\n{\n";
+    o << "    extern __shared__ __align__(16) u64 sm[];\n";
+    o << "    float *sacc = reinterpret_cast<float *>(sm + " << (size_t(1) << p.k) << ");\n";
+    o << "    const u32 tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;\n";
+    o << "    for (int q = tid; q < " << 2 * nslots * (T / 32) << "; q += " << T << ") sacc[q] = 0.f;\n";
+    o << "    __syncthreads();\n";
+    auto phys_mask = [&](const int8_t *Q) {
+        std::vector<uint64_t> m(G.nq);
+        for (int b = 0; b < G.nq; ++b) m[b] = G.phys(1u << Q[b]);
+        return m;
+    };
+    auto word_mask = [&](const int8_t *Q) {
+        std::vector<uint64_t> m(G.nq);
+        for (int b = 0; b < G.nq; ++b) m[b] = swz8((1u << Q[b]) >> 1);
+        return m;
+    };
+    const plan::Stage &s0 = p.stages.front(), &sl = p.stages.back();
+    o << "    const u64 gL = " << thread_expr(phys_mask(s0.in.Q), true) << ";\n";
+    o << "    const u64 gS = " << thread_expr(phys_mask(sl.out.Q), true) << ";\n";
+    for (size_t s = 1; s < p.stages.size(); ++s) {
+        o << "    const u32 wW" << s << " = " << thread_expr(word_mask(p.stages[s - 1].out.Q), false) << ";\n";
+        o << "    const u32 wR" << s << " = " << thread_expr(word_mask(p.stages[s].in.Q), false) << ";\n";
+    }
+    o << "    for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {\n";
+    o << "    const u64 base = 0ull";
+    for (int s = 0; s < p.nseg; ++s)
+        o << " | (((t >> " << p.seg_src[s] << ") & " << hex64((uint64_t(1) << p.seg_w[s]) - 1) << ") << "
+          << p.seg_dst[s] << ")";
+    o << ";\n";
+    auto reg_offset = [&](const int8_t *P, int v) {
+        uint32_t l = 0;
+        for (int j = 0; j < 3; ++j)
+            if ((v >> j) & 1) l |= 1u << P[j];
+        return l;
+    };
+    o << "    u64 r[8], i[8], rl[8], il[8];\n";
+    for (int b = 0; b < 2; ++b) {
+        const char *src = b ? "lam" : "amp";
+        const char *R = b ? "rl" : "r", *I = b ? "il" : "i";
+        o << "    { const float *a = " << src << " + 2 * (base + gL);\n";
+        for (int v = 0; v < 8; ++v)
+            o << "      const float4 f" << v << " = *reinterpret_cast<const float4 *>(a + 2 * "
+              << hex64(G.phys(reg_offset(s0.in.P, v))) << ");\n";
+        for (int v = 0; v < 8; ++v)
+            o << "      " << R << "[" << v << "] = pk(f" << v << ".x, f" << v << ".z); " << I << "[" << v << "] = pk(f" << v
+              << ".y, f" << v << ".w);\n";
+        o << "    }\n";
+    }
+    for (size_t s = 0; s < p.stages.size(); ++s) {
+        const plan::Stage &st = p.stages[s];
+        if (s > 0) {
+            const plan::Stage &pr = p.stages[s - 1];
+            // psi through words [0, 2^k / 2) x 2 halves, lambda through the next 2^k words
+            o << "    { u64 *pre = sm, *pim = sm + " << (1 << (p.k - 1)) << ";\n";
+            for (int v = 0; v < 8; ++v) {
+                const uint32_t w = swz8(reg_offset(pr.out.P, v) >> 1);
+                o << "      pre[wW" << s << " ^ " << hex32(w) << "] = r[" << v << "]; pim[wW" << s << " ^ " << hex32(w)
+                  << "] = i[" << v << "];\n";
+            }
+            o << "      __syncthreads();\n";
+            for (int v = 0; v < 8; ++v) {
+                const uint32_t w = swz8(reg_offset(st.in.P, v) >> 1);
+                o << "      r[" << v << "] = pre[wR" << s << " ^ " << hex32(w) << "]; i[" << v << "] = pim[wR" << s
+                  << " ^ " << hex32(w) << "];\n";
+            }
+            o << "      __syncthreads();\n";
+            for (int v = 0; v < 8; ++v) {
+                const uint32_t w = swz8(reg_offset(pr.out.P, v) >> 1);
+                o << "      pre[wW" << s << " ^ " << hex32(w) << "] = rl[" << v << "]; pim[wW" << s << " ^ " << hex32(w)
+                  << "] = il[" << v << "];\n";
+            }
+            o << "      __syncthreads();\n";
+            for (int v = 0; v < 8; ++v) {
+                const uint32_t w = swz8(reg_offset(st.in.P, v) >> 1);
+                o << "      rl[" << v << "] = pre[wR" << s << " ^ " << hex32(w) << "]; il[" << v << "] = pim[wR" << s
+                  << " ^ " << hex32(w) << "];\n";
+            }
+            o << "      __syncthreads(); }\n";
+        }
+        for (int k = st.op_begin; k < st.op_end; ++k) emit_adj_op_c64(o, p.ops[k], coff[k], lsl[k]);
+    }
+    for (int b = 0; b < 2; ++b) {
+        const char *dst = b ? "lam" : "amp";
+        const char *R = b ? "rl" : "r", *I = b ? "il" : "i";
+        o << "    { float *a = " << dst << " + 2 * (base + gS); float x0, x1, y0, y1;\n";
+        for (int v = 0; v < 8; ++v)
+            o << "      upk(" << R << "[" << v << "], x0, x1); upk(" << I << "[" << v
+              << "], y0, y1); *reinterpret_cast<float4 *>(a + 2 * " << hex64(G.phys(reg_offset(sl.out.P, v)))
+              << ") = make_float4(x0, y0, x1, y1);\n";
+        o << "    }\n";
+    }
+    o << "    }\n";
+    o << "    __syncthreads();\n";
+    o << "    for (int q = tid; q < " << nslots << "; q += " << T << ") {\n";
+    o << "        double v = 0;\n";
+    o << "        for (int w = 0; w < NW; ++w) v += double(sacc[2 * (q * NW + w)]) + double(sacc[2 * (q * NW + w) + 1]);\n";
+    o << "        part[(size_t)cf.gslot[q] * Gc + blockIdx.x] = 2.0 * v;  // 2 Re <lambda | D psi>\n";
+    o << "    }\n}\n";
+    return o.str();
+}
+
 // ---------------------------------------------------------------- compile + cache
 struct Compiled {
     CUmodule mod = nullptr;
@@ -559,22 +790,24 @@ bool jit_available(std::string *why)
     return N.ok;
 }
 
-qv_status jit_run_plan(qv_state *s, const std::vector<plan::Pass> &passes)
+namespace {
+
+// Kernels `entry` of srcs[i] (dynamic shared memory smem[i], threads[i] per
+// CTA), compiled in parallel host threads or taken from the process-wide cache.
+qv_status get_kernels(qv_state *s, const std::vector<std::string> &srcs, const char *entry,
+                      const std::vector<size_t> &smem, const std::vector<int> &threads,
+                      std::vector<std::shared_ptr<Compiled>> &fns)
 {
-    const bool c64 = s->dt == QV_C64;
     std::string why;
-    if (!jit_available(&why)) return fail(QV_ERR_UNSUPPORTED, "compiled fused passes unavailable: %s", why.c_str());
+    if (!jit_available(&why)) return fail(QV_ERR_UNSUPPORTED, "compiled passes unavailable: %s", why.c_str());
     // make sure this thread has the device's primary context current for the driver API
     QV_CUDA(cudaSetDevice(s->device));
     QV_CUDA(cudaFree(nullptr));
-
-    std::vector<std::string> srcs(passes.size());
-    std::vector<std::shared_ptr<Compiled>> fns(passes.size());
+    fns.assign(srcs.size(), nullptr);
     std::vector<size_t> todo;
     {
         std::lock_guard<std::mutex> lock(g_cache_mu);
-        for (size_t i = 0; i < passes.size(); ++i) {
-            srcs[i] = gen_source(passes[i], c64);
+        for (size_t i = 0; i < srcs.size(); ++i) {
             auto it = g_cache.find({s->device, srcs[i]});
             if (it != g_cache.end()) fns[i] = it->second;
             else if (std::find_if(todo.begin(), todo.end(), [&](size_t j) { return srcs[j] == srcs[i]; }) == todo.end())
@@ -604,27 +837,44 @@ qv_status jit_run_plan(qv_state *s, const std::vector<plan::Pass> &passes)
         for (auto &t : th) t.join();
         std::lock_guard<std::mutex> lock(g_cache_mu);
         for (size_t j = 0; j < todo.size(); ++j) {
-            if (!okv[j]) return fail(QV_ERR_CUDA, "compiling a fused pass failed: %s", errs[j].c_str());
+            if (!okv[j]) return fail(QV_ERR_CUDA, "compiling a pass failed: %s", errs[j].c_str());
             auto c = std::make_shared<Compiled>();
             const JitApi &A = api();
             CUresult r = A.module_load(&c->mod, cubins[j].data());
             if (r != CUDA_SUCCESS) return cu_fail(r, "cuModuleLoadData");
-            r = A.get_function(&c->fn, c->mod, "qv_pass");
+            r = A.get_function(&c->fn, c->mod, entry);
             if (r != CUDA_SUCCESS) return cu_fail(r, "cuModuleGetFunction");
-            const int k = passes[todo[j]].k;
-            c->smem = (c64 ? 8 : 16) * (size_t(1) << k);
+            c->smem = smem[todo[j]];
             if (c->smem > 48 * 1024) {
                 r = A.set_attr(c->fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, int(c->smem));
                 if (r != CUDA_SUCCESS) return cu_fail(r, "cuFuncSetAttribute");
             }
-            r = A.occupancy(&c->per_sm, c->fn, 1 << (k - kRegBits), c->smem);
+            r = A.occupancy(&c->per_sm, c->fn, threads[todo[j]], c->smem);
             if (r != CUDA_SUCCESS) return cu_fail(r, "cuOccupancyMaxActiveBlocksPerMultiprocessor");
             if (c->per_sm < 1) return fail(QV_ERR_UNSUPPORTED, "compiled pass does not fit on an SM");
             g_cache[{s->device, srcs[todo[j]]}] = c;
         }
-        for (size_t i = 0; i < passes.size(); ++i)
+        for (size_t i = 0; i < srcs.size(); ++i)
             if (!fns[i]) fns[i] = g_cache[{s->device, srcs[i]}];
     }
+    return QV_OK;
+}
+
+}  // namespace
+
+qv_status jit_run_plan(qv_state *s, const std::vector<plan::Pass> &passes)
+{
+    const bool c64 = s->dt == QV_C64;
+    std::vector<std::string> srcs(passes.size());
+    std::vector<size_t> smem(passes.size());
+    std::vector<int> threads(passes.size());
+    for (size_t i = 0; i < passes.size(); ++i) {
+        srcs[i] = gen_source(passes[i], c64);
+        smem[i] = (c64 ? 8 : 16) * (size_t(1) << passes[i].k);
+        threads[i] = 1 << (passes[i].k - kRegBits);
+    }
+    std::vector<std::shared_ptr<Compiled>> fns;
+    QV_TRY(get_kernels(s, srcs, "qv_pass", smem, threads, fns));
     // launch every pass with its coefficients as a by-value parameter
     std::vector<uint64_t> coef;
     for (size_t i = 0; i < passes.size(); ++i) {
@@ -645,11 +895,62 @@ qv_status jit_run_plan(qv_state *s, const std::vector<plan::Pass> &passes)
         void *args[] = {&amp, const_cast<uint64_t *>(&ntiles), coef.data()};
         prof_bytes(s, QV_K_FUSED, 2.0 * double(dim(s)) * amp_bytes(s->dt));
         prof_begin(s, QV_K_FUSED);
-        const CUresult r = api().launch(c.fn, grid, 1, 1, 1u << (p.k - kRegBits), 1, 1, unsigned(c.smem),
+        const CUresult r = api().launch(c.fn, grid, 1, 1, unsigned(threads[i]), 1, 1, unsigned(c.smem),
                                           reinterpret_cast<CUstream>(s->stream), args, nullptr);
         prof_end(s, QV_K_FUSED);
         if (r != CUDA_SUCCESS) return cu_fail(r, "cuLaunchKernel");
         s->prof.h2d += coef.size() * sizeof(uint64_t);
+    }
+    return QV_OK;
+}
+
+qv_status jit_run_adjoint(qv_state *s, const std::vector<plan::Pass> &passes, void *lam, double *part, int G)
+{
+    if (s->dt != QV_C64) return fail(QV_ERR_UNSUPPORTED, "compiled adjoint passes are complex64 only");
+    std::vector<std::string> srcs(passes.size());
+    std::vector<size_t> smem(passes.size());
+    std::vector<int> threads(passes.size()), nslots(passes.size(), 0);
+    for (size_t i = 0; i < passes.size(); ++i) {
+        for (const plan::Op &op : passes[i].ops) nslots[i] += op.nd;
+        srcs[i] = gen_source_adj(passes[i], nslots[i]);
+        threads[i] = 1 << (passes[i].k - kRegBits);
+        smem[i] = 8 * (size_t(1) << passes[i].k) + size_t(2 * sizeof(float)) * nslots[i] * (threads[i] / 32);
+    }
+    std::vector<std::shared_ptr<Compiled>> fns;
+    QV_TRY(get_kernels(s, srcs, "qv_adj", smem, threads, fns));
+    std::vector<uint64_t> args_buf;
+    for (size_t i = 0; i < passes.size(); ++i) {
+        const plan::Pass &p = passes[i];
+        size_t total = 0;
+        for (const plan::Op &op : p.ops) total += size_t(coef_slots_adj(op));
+        total = std::max<size_t>(1, total);
+        const size_t ns = std::max(1, nslots[i]);
+        args_buf.assign(total + (ns + 1) / 2, 0);  // QvAdjArgs: u64 c[total]; int gslot[ns]
+        size_t off = 0;
+        int32_t *gslot = reinterpret_cast<int32_t *>(args_buf.data() + total);
+        int lsl = 0;
+        for (const plan::Op &op : p.ops) {
+            op_coeffs_c64(op, args_buf.data() + off);
+            for (int d = 0; d < op.nd; ++d) {
+                for (int e = 0; e < 4; ++e)
+                    lane_triple(args_buf.data() + off + 24 + 12 * d + 3 * e, op.sreg == 3 ? cd(0.0) : op.D[d][e],
+                                op.D[d][e]);
+                gslot[lsl++] = op.slot + d;
+            }
+            off += size_t(coef_slots_adj(op));
+        }
+        const Compiled &c = *fns[i];
+        const uint64_t ntiles = dim(s) >> p.k;
+        const unsigned grid = unsigned(std::min<uint64_t>({ntiles, uint64_t(c.per_sm) * s->num_sms, uint64_t(G)}));
+        void *amp = s->amp;
+        void *args[] = {&amp, &lam, const_cast<uint64_t *>(&ntiles), &part, &G, args_buf.data()};
+        prof_bytes(s, QV_K_ADJOINT, 4.0 * double(dim(s)) * amp_bytes(s->dt));
+        prof_begin(s, QV_K_ADJOINT);
+        const CUresult r = api().launch(c.fn, grid, 1, 1, unsigned(threads[i]), 1, 1, unsigned(c.smem),
+                                          reinterpret_cast<CUstream>(s->stream), args, nullptr);
+        prof_end(s, QV_K_ADJOINT);
+        if (r != CUDA_SUCCESS) return cu_fail(r, "cuLaunchKernel");
+        s->prof.h2d += args_buf.size() * sizeof(uint64_t);
     }
     return QV_OK;
 }

@@ -9,6 +9,7 @@ namespace plan {
 namespace {
 
 constexpr int kMaxOpsPerPass = 160;
+constexpr int kMaxOpsAdjoint = 60;  // adjoint plans: ops carry derivatives (coefficient space)
 constexpr int kMaxStagesPerPass = 40;
 constexpr int kLookahead = 96;  // gates scanned when ranking candidate tile qubits
 
@@ -377,6 +378,9 @@ bool make_plan(int n, int k, bool pin0, bool fuse, bool pairs, const std::vector
     }
     std::vector<int> rem(gates.size());
     for (size_t i = 0; i < gates.size(); ++i) rem[i] = int(i);
+    bool adjoint = false;
+    for (const PGate &g : gates) adjoint |= g.nd > 0;
+    const int max_ops = adjoint ? kMaxOpsAdjoint : kMaxOpsPerPass;
     const int first_free = pin0 ? 6 : 5;  // lowest position a canonical register bit may take
 
     while (!rem.empty()) {
@@ -509,7 +513,7 @@ bool make_plan(int n, int k, bool pin0, bool fuse, bool pairs, const std::vector
         auto process = [&](const PGate &g) {
             const int t = g.t, c = g.c;
             const bool nondiag = g.cls != G_DIAG;
-            const int o = fuse ? open_op[t] : -1;
+            const int o = (fuse && g.nd == 0) ? open_op[t] : -1;
             bool fused = false;
             if (o >= 0) {
                 Op &op = ops[o];
@@ -554,7 +558,11 @@ bool make_plan(int n, int k, bool pin0, bool fuse, bool pairs, const std::vector
                 }
                 op.m0id = c >= 0 ? 1 : 0;
                 if (c >= 0) coord(c, op.sreg, op.sthr, op.sext);
-                open_op[t] = int(ops.size());
+                op.nd = g.nd;
+                op.slot = g.slot;
+                for (int d = 0; d < g.nd; ++d)
+                    for (int e = 0; e < 4; ++e) op.D[d][e] = g.dU[d][e];
+                open_op[t] = g.nd > 0 ? -1 : int(ops.size());  // nothing merges into a differentiated op
                 op_sel.push_back(c);
                 op_time.push_back(gtime);
                 ops.push_back(op);
@@ -579,7 +587,7 @@ bool make_plan(int n, int k, bool pin0, bool fuse, bool pairs, const std::vector
                 bool blk = false;
                 for (int i = 0; i < nq; ++i) blk |= blocked[qs[i]] != 0;
                 bool exec = false;
-                if (!blk && int(ops.size()) < kMaxOpsPerPass) {
+                if (!blk && int(ops.size()) < max_ops) {
                     if (g.cls == G_DIAG || g.cls == G_SWAP) exec = true;
                     else exec = ls.reg_of(pos_of[g.t]) >= 0;
                 }
@@ -601,7 +609,7 @@ bool make_plan(int n, int k, bool pin0, bool fuse, bool pairs, const std::vector
             }
             left.swap(still);
             if (left.empty()) break;
-            if (int(ops.size()) >= kMaxOpsPerPass || int(stages.size()) + 2 >= kMaxStagesPerPass) break;
+            if (int(ops.size()) >= max_ops || int(stages.size()) + 2 >= kMaxStagesPerPass) break;
             // the first gate left needs a register bit it lacks: new register set
             cur.out = ls.L;
             cur.op_end = int(ops.size());

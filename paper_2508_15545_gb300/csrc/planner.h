@@ -40,6 +40,11 @@ struct PGate {
     int cls;          // GateClass
     int t, t2, c;     // target, swap partner (-1), control (-1)
     std::complex<double> U[4];
+    // Adjoint plans only: nd > 0 marks a gate whose derivatives dU[0..nd) are
+    // evaluated where it runs (first gradient slot `slot`). Such a gate gets an
+    // op of its own (class G_GEN), never merged with other gates.
+    int nd = 0, slot = -1;
+    std::complex<double> dU[3][4];
 };
 
 enum OpType : int8_t { OP_GEN = 0, OP_X = 1, OP_DIAG = 2, OP_GEN2 = 3 };
@@ -65,6 +70,8 @@ struct Op {
     uint64_t text;    // DIAG: target physical qubit outside the tile (0: none)
     std::complex<double> M[2][4];   // row-major 2x2 for s = 0 / 1 (DIAG: entries [0], [3])
     std::complex<double> M4[16];    // GEN2 only
+    int nd = 0, slot = -1;          // adjoint plans: derivatives of this op's gate (see PGate)
+    std::complex<double> D[3][4];   // derivative matrices, applied where M[1] applies
 };
 
 struct Layout {

@@ -407,14 +407,14 @@ qv_status qv_apply_pauli(qv_state *s, const qv_pauli_term *terms, size_t nt, qv_
 qv_status qv_adjoint_grad(qv_state *s, const qv_gate *g, size_t ng, const qv_pauli_term *H, size_t nt,
                           size_t nparams, double *grad_out, double *expval_out)
 {
-    return qv_adjoint_grad_ex(s, g, ng, H, nt, nparams, grad_out, expval_out, QV_MODE_AUTO);
+    return qv_adjoint_grad_ex(s, g, ng, H, nt, nparams, grad_out, expval_out, QV_SWEEP_AUTO);
 }
 
 qv_status qv_adjoint_grad_ex(qv_state *s, const qv_gate *g, size_t ng, const qv_pauli_term *H, size_t nt,
                              size_t nparams, double *grad_out, double *expval_out, int32_t sweep_mode)
 {
     CHECK_HANDLE(s);
-    if (sweep_mode != QV_MODE_AUTO && sweep_mode != QV_MODE_PLAIN && sweep_mode != QV_MODE_FUSED)
+    if (sweep_mode < QV_SWEEP_AUTO || sweep_mode > QV_SWEEP_COMPILED)
         return fail(QV_ERR_ARG, "bad sweep mode %d", int(sweep_mode));
     if (ng && !g) return fail(QV_ERR_ARG, "gate list is NULL");
     if (nt && !H) return fail(QV_ERR_ARG, "terms is NULL");
@@ -435,7 +435,7 @@ qv_status qv_adjoint_grad_ex(qv_state *s, const qv_gate *g, size_t ng, const qv_
                 return fail(QV_ERR_ARG, "gate %zu: parameter index %d >= nparams", l, G.param[a]);
         }
     }
-    return adjoint_grad(s, g, ng, H, nt, nparams, grad_out, expval_out, sweep_mode != QV_MODE_PLAIN);
+    return adjoint_grad(s, g, ng, H, nt, nparams, grad_out, expval_out, sweep_mode);
 }
 
 qv_status qv_autotune(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t *best_tile_bits)

@@ -130,10 +130,9 @@ qv_status validate_gate(const qv_gate &g, int n, size_t idx);
 // ---------------------------------------------------------------- adjoint (adjoint.cu)
 // dst = H src for H = sum of Pauli terms; src, dst: 2^n amplitudes of s's dtype.
 qv_status pauli_apply(qv_state *s, const void *src, void *dst, const qv_pauli_term *terms, size_t nt);
-// tiled = true: the reverse sweep runs in tiled passes (n >= 10), else one
-// pass over both buffers per gate.
+// sweep: QV_SWEEP_* (qv.h)
 qv_status adjoint_grad(qv_state *s, const qv_gate *g, size_t ng, const qv_pauli_term *H, size_t nt, size_t nparams,
-                       double *grad_out, double *expval_out, bool tiled);
+                       double *grad_out, double *expval_out, int sweep);
 void adjoint_release(qv_state *s);
 
 // ---------------------------------------------------------------- verification (verify.cu)

@@ -14,5 +14,10 @@ bool jit_available(std::string *why);
 // Compiles (or takes from the process-wide cache) one kernel per pass and
 // launches the passes in order on the handle's stream.
 qv_status jit_run_plan(qv_state *s, const std::vector<plan::Pass> &passes);
+// Reverse sweep of the adjoint gradient (complex64): plan of the daggered
+// gates in reverse order; an op with derivatives (Op::nd > 0) writes its
+// partials 2 Re <lambda | D psi> to part[slot * G + CTA]; part columns of CTAs
+// not launched are left untouched.
+qv_status jit_run_adjoint(qv_state *s, const std::vector<plan::Pass> &passes, void *lam, double *part, int G);
 
 }  // namespace qv

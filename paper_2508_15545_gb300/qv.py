@@ -21,6 +21,7 @@ QV_MODE_AUTO, QV_MODE_PLAIN, QV_MODE_FUSED = 0, 1, 2
 QV_PLAN_NO_FUSION = 1
 QV_PLAN_INTERPRET = 2
 QV_PLAN_NO_PAIRS = 4
+QV_SWEEP_AUTO, QV_SWEEP_PER_GATE, QV_SWEEP_TILES, QV_SWEEP_COMPILED = 0, 1, 2, 3
 STATUS_NAMES = {0: "QV_OK", 1: "QV_ERR_ARG", 2: "QV_ERR_OOM", 3: "QV_ERR_CUDA",
                 4: "QV_ERR_TIMEOUT", 5: "QV_ERR_UNSUPPORTED"}
 KIND = {"h": 0, "x": 1, "y": 2, "z": 3, "s": 4, "sdg": 5, "t": 6, "tdg": 7,
@@ -312,10 +313,10 @@ def qv_apply_pauli(h: int, terms, out_h: int):
     _check(lib.qv_apply_pauli(h, terms_to_c(terms), len(terms), out_h))
 
 
-def qv_adjoint_grad(h: int, gates, terms, nparams: int, sweep_mode: int = QV_MODE_AUTO):
+def qv_adjoint_grad(h: int, gates, terms, nparams: int, sweep_mode: int = QV_SWEEP_AUTO):
     """Adjoint-method gradient of <H> over the circuit ``gates`` applied to the
-    handle's current state. Returns (grad as numpy array, <H>). ``sweep_mode``:
-    QV_MODE_PLAIN = one pass per gate, QV_MODE_FUSED / AUTO = tiled passes."""
+    handle's current state. Returns (grad as numpy array, <H>). ``sweep_mode``
+    is one of QV_SWEEP_* (per gate, shared-memory tiles, compiled passes)."""
     if isinstance(gates, tuple) and len(gates) == 2 and isinstance(gates[1], int):
         arr, ng = gates
     else:

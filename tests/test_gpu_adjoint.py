@@ -67,8 +67,8 @@ def test_adjoint_mixed_gates(qvlib, orc, cuda, dtype):
     assert np.linalg.norm(after.astype(complex) - before.astype(complex)) <= (1e-5 if dtype == 0 else 1e-12)
 
 
-# sweep: 1 = one pass per gate, 2 = tiled passes
-@pytest.mark.parametrize("sweep", [1, 2])
+# sweep: 1 = one pass per gate, 2 = shared-memory tiles, 3 = compiled passes (complex64)
+@pytest.mark.parametrize("sweep", [1, 2, 3])
 @pytest.mark.parametrize("dtype", [0, 1])
 def test_adjoint_ansatz_12q_vs_param_shift_and_fd(qvlib, orc, cuda, dtype, sweep):
     """12-qubit copy of the 26-qubit gradient workload: 16 layers of RY, RZ and
@@ -157,14 +157,15 @@ def test_adjoint_tiled_sweep_mixed(qvlib, orc, cuda, dtype, n):
     gates, npar = _mixed_trainable(n, 70, seed=400 + n)
     terms = W.ansatz_hamiltonian(n) + [(0.35, 0b1010, 0b0110), (-0.2, 0, (1 << n) - 1)]
     psi0 = W.random_state(n, 9 + n)
-    g2, e2, before, after = _adjoint(qv, n, dtype, gates, terms, npar, psi0, sweep=2)
     g1, e1, _, _ = _adjoint(qv, n, dtype, gates, terms, npar, psi0, sweep=1)
     ref = orc.param_shift_grad(n, gates, terms, npar, psi0)
     tol = 2e-4 if dtype == 0 else 1e-10
-    assert e2 == pytest.approx(orc.energy(n, gates, terms, psi0), abs=tol)
-    assert np.max(np.abs(g2 - ref)) <= tol
-    assert np.max(np.abs(g2 - g1)) <= tol
-    assert np.linalg.norm(after.astype(complex) - before.astype(complex)) <= (2e-5 if dtype == 0 else 1e-12)
+    for sweep in (2, 3):
+        g2, e2, before, after = _adjoint(qv, n, dtype, gates, terms, npar, psi0, sweep=sweep)
+        assert e2 == pytest.approx(orc.energy(n, gates, terms, psi0), abs=tol)
+        assert np.max(np.abs(g2 - ref)) <= tol, sweep
+        assert np.max(np.abs(g2 - g1)) <= tol, sweep
+        assert np.linalg.norm(after.astype(complex) - before.astype(complex)) <= (2e-5 if dtype == 0 else 1e-12)
 
 
 @pytest.mark.parametrize("dtype", [0, 1])
@@ -183,7 +184,8 @@ def test_adjoint_tiled_zero_angles(qvlib, orc, cuda, dtype):
               Gate("u3", 13, theta=(0.7, 0.1, 0.2), param=(7, -1, 8))]
     terms = [(1.0, 1 << 13, 0), (0.5, 1 << 12, 1 << 11), (0.25, 0, (1 << 10) | (1 << 9)), (0.3, 1 << 11, 0)]
     psi0 = W.random_state(n, 123)
-    g, e, _, _ = _adjoint(qv, n, dtype, gates, terms, 9, psi0, sweep=2)
     ref = orc.param_shift_grad(n, gates, terms, 9, psi0)
     tol = 1e-4 if dtype == 0 else 1e-10
-    assert np.max(np.abs(g - ref)) <= tol, (g, ref)
+    for sweep in (2, 3):
+        g, e, _, _ = _adjoint(qv, n, dtype, gates, terms, 9, psi0, sweep=sweep)
+        assert np.max(np.abs(g - ref)) <= tol, (sweep, g, ref)
