@@ -195,6 +195,52 @@ template <int J, int C, int S> QI float gd_reg(const u64 (&r)[8], const u64 (&i)
     }
     float a0, a1; upk(acc, a0, a1); return a0 + a1;
 }
+// real 2x2 (imaginary parts zero): (re, re) pairs of U00 U01 U10 U11 at c[0], c[3], c[6], c[9]
+QI void ap2r(const u64 (&c)[12], u64 &ar, u64 &ai, u64 &br, u64 &bi) {
+    const u64 xr = ar, xi = ai, yr = br, yi = bi;
+    ar = f2fma(c[0], xr, f2mul(c[3], yr)); ai = f2fma(c[0], xi, f2mul(c[3], yi));
+    br = f2fma(c[6], xr, f2mul(c[9], yr)); bi = f2fma(c[6], xi, f2mul(c[9], yi));
+}
+template <int J, int C, int S> QI void g_real(u64 (&r)[8], u64 (&i)[8], const u64 (&c)[12]) {
+#pragma unroll
+    for (int v = 0; v < 8; ++v)
+        if (!((v >> J) & 1) && (C < 0 || ((v >> C) & 1) == S)) ap2r(c, r[v], i[v], r[v | (1 << J)], i[v | (1 << J)]);
+}
+template <int J, int C, int S> QI float gd_real(const u64 (&r)[8], const u64 (&i)[8], const u64 (&lr)[8],
+                                                const u64 (&li)[8], const u64 (&d)[12]) {
+    u64 acc = 0ull;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        if ((v >> J) & 1) continue;
+        if (C >= 0 && ((v >> C) & 1) != S) continue;
+        const int w = v | (1 << J);
+        u64 xr = r[v], xi = i[v], yr = r[w], yi = i[w];
+        ap2r(d, xr, xi, yr, yi);
+        acc = f2fma(lr[v], xr, acc); acc = f2fma(li[v], xi, acc);
+        acc = f2fma(lr[w], yr, acc); acc = f2fma(li[w], yi, acc);
+    }
+    float a0, a1; upk(acc, a0, a1); return a0 + a1;
+}
+// diagonal 2x2 in the general layout: d0 = c[0..2] (U00), d1 = c[9..11] (U11)
+template <int J, int C, int S> QI void g_diag(u64 (&r)[8], u64 (&i)[8], const u64 (&c)[12]) {
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        if (C >= 0 && ((v >> C) & 1) != S) continue;
+        if ((v >> J) & 1) cm2(c[9], c[10], c[11], r[v], i[v]); else cm2(c[0], c[1], c[2], r[v], i[v]);
+    }
+}
+template <int J, int C, int S> QI float gd_diag(const u64 (&r)[8], const u64 (&i)[8], const u64 (&lr)[8],
+                                                const u64 (&li)[8], const u64 (&d)[12]) {
+    u64 acc = 0ull;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        if (C >= 0 && ((v >> C) & 1) != S) continue;
+        u64 xr = r[v], xi = i[v];
+        if ((v >> J) & 1) cm2(d[9], d[10], d[11], xr, xi); else cm2(d[0], d[1], d[2], xr, xi);
+        acc = f2fma(lr[v], xr, acc); acc = f2fma(li[v], xi, acc);
+    }
+    float a0, a1; upk(acc, a0, a1); return a0 + a1;
+}
 // the same for a target on the packed lane (tile qubit 0): scalar pairs
 template <int C, int S> QI float gd_lane(const u64 (&r)[8], const u64 (&i)[8], const u64 (&lr)[8],
                                          const u64 (&li)[8], const u64 (&d)[12]) {
@@ -577,7 +623,22 @@ void emit_adj_op_c64(std::ostream &o, const plan::Op &op, int O, int lslot)
     const int J = op.treg, C = op.sreg;
     std::string apply, grad;
     int s = 0;
-    if (C < 0) {
+    // cheaper forms for a register target: diagonal (RZ, P) or real (RY) matrix and derivatives
+    const int b = op.m0id ? 1 : 0;  // the branch that is not the identity
+    bool diag = J < 3, real = J < 3;
+    for (int d = -1; d < op.nd; ++d) {
+        const std::complex<double> *m = d < 0 ? op.M[b] : op.D[d];
+        diag &= m[1] == 0.0 && m[2] == 0.0;
+        for (int e = 0; e < 4; ++e) real &= m[e].imag() == 0.0;
+    }
+    if (C == 3) diag = real = false;  // lane-resolved coefficients differ per lane
+    if (diag || real) {
+        const std::string f = diag ? "diag" : "real";
+        const std::string cc = C < 0 ? "-1, 0" : std::to_string(C) + ", 1";
+        if (C >= 0) s = 1;
+        apply = "g_" + f + "<" + std::to_string(J) + ", " + cc + ">(r, i, c);";
+        grad = "gd_" + f + "<" + std::to_string(J) + ", " + cc + ">";
+    } else if (C < 0) {
         apply = J < 3 ? "g_all<" + std::to_string(J) + ">(r, i, c);" : "g_lane<-1, 0>(r, i, c);";
         grad = J < 3 ? "gd_reg<" + std::to_string(J) + ", -1, 0>" : "gd_lane<-1, 0>";
     } else if (C == 3) {  // select on the packed lane: coefficients resolved per lane
