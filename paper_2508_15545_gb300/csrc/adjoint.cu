@@ -29,6 +29,9 @@ struct AdjointBuffers {
     size_t lam_bytes = 0;
     double *part = nullptr;    // per-block partial sums
     size_t part_count = 0;
+    // compiled reverse sweep of the last gate list (same bytes: no re-planning)
+    std::vector<qv_gate> key;
+    std::shared_ptr<JitProgram> sweep;
 };
 
 namespace {
@@ -803,6 +806,11 @@ qv_status adjoint_sweep_tiled(qv_state *s, const qv_gate *g, size_t ng, const st
 qv_status adjoint_sweep_compiled(qv_state *s, const qv_gate *g, size_t ng, const std::vector<int> &gate_slot,
                                  double *part, int G)
 {
+    AdjointBuffers &B = *s->adj;
+    if (B.sweep && B.key.size() == ng && std::memcmp(B.key.data(), g, ng * sizeof(qv_gate)) == 0)
+        return jit_launch_adjoint(s, *B.sweep, B.lam, part, G);
+    B.key.clear();
+    B.sweep.reset();
     std::vector<plan::PGate> pg;
     pg.reserve(ng);
     for (size_t l = ng; l-- > 0;) {
@@ -837,7 +845,9 @@ qv_status adjoint_sweep_compiled(qv_state *s, const qv_gate *g, size_t ng, const
     const int K = std::min(s->n, plan::kMaxK);
     if (!plan::make_plan(s->n, K, true, true, false, pg, passes, st, err))
         return fail(QV_ERR_UNSUPPORTED, "planner: %s", err.c_str());
-    return jit_run_adjoint(s, passes, s->adj->lam, part, G);
+    QV_TRY(jit_prepare_adjoint(s, passes, B.sweep));
+    B.key.assign(g, g + ng);
+    return jit_launch_adjoint(s, *B.sweep, B.lam, part, G);
 }
 
 template <typename R>

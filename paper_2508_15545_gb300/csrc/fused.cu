@@ -27,8 +27,15 @@
 namespace qv {
 
 struct PlanCache {
-    void *dev = nullptr;
+    void *dev = nullptr;   // interpreter programs on the device
     size_t bytes = 0;
+    // the last gate list planned on this handle, its plan and compiled program:
+    // applying the same list again (same bytes, tile size and flags) skips the
+    // planning and the code generation
+    std::vector<qv_gate> key;
+    int K = 0, flags = 0;
+    std::vector<plan::Pass> passes;
+    std::shared_ptr<JitProgram> jit;
 };
 
 namespace {
@@ -211,20 +218,33 @@ qv_status apply_fused(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_op
     int K = (opts && opts->tile_bits) ? opts->tile_bits : default_tile_bits(s, opts);
     if (K < plan::kMinK || K > plan::kMaxK) return fail(QV_ERR_ARG, "tile_bits %d outside [10, 12]", K);
     if (K > s->n) return fail(QV_ERR_ARG, "tile_bits %d exceeds n = %d", K, s->n);
-    std::vector<plan::PGate> pg;
-    QV_TRY(to_pgates(g, ng, pg));
-    std::vector<plan::Pass> passes;
-    plan::PlanStats st;
-    std::string err;
     const int flags = opts ? opts->flags : 0;
     const bool fuse = !(flags & QV_PLAN_NO_FUSION);
     const bool jit = !(flags & QV_PLAN_INTERPRET) && jit_available(nullptr);
-    // 4x4 operations exist only in the compiled complex64 kernel
-    const bool pairs = jit && s->dt == QV_C64 && !(flags & QV_PLAN_NO_PAIRS);
-    if (!plan::make_plan(s->n, K, s->dt == QV_C64, fuse, pairs, pg, passes, st, err))
-        return fail(QV_ERR_UNSUPPORTED, "planner: %s", err.c_str());
-    if (jit) return jit_run_plan(s, passes);
-    return s->dt == QV_C64 ? run_plan<float>(s, passes, K) : run_plan<double>(s, passes, K);
+    if (!s->plan) s->plan = new PlanCache;
+    PlanCache &C = *s->plan;
+    const bool hit = C.K == K && C.flags == flags && C.key.size() == ng &&
+                     std::memcmp(C.key.data(), g, ng * sizeof(qv_gate)) == 0;
+    if (!hit) {
+        std::vector<plan::PGate> pg;
+        QV_TRY(to_pgates(g, ng, pg));
+        std::vector<plan::Pass> passes;
+        plan::PlanStats st;
+        std::string err;
+        // 4x4 operations exist only in the compiled complex64 kernel
+        const bool pairs = jit && s->dt == QV_C64 && !(flags & QV_PLAN_NO_PAIRS);
+        if (!plan::make_plan(s->n, K, s->dt == QV_C64, fuse, pairs, pg, passes, st, err))
+            return fail(QV_ERR_UNSUPPORTED, "planner: %s", err.c_str());
+        C.key.clear();  // invalid until the new plan is complete
+        C.passes = std::move(passes);
+        C.jit.reset();
+        if (jit) QV_TRY(jit_prepare(s, C.passes, C.jit));
+        C.key.assign(g, g + ng);
+        C.K = K;
+        C.flags = flags;
+    }
+    if (jit) return jit_launch(s, *C.jit);
+    return s->dt == QV_C64 ? run_plan<float>(s, C.passes, K) : run_plan<double>(s, C.passes, K);
 }
 
 qv_status apply_permutation(qv_state *s, const int32_t *perm)

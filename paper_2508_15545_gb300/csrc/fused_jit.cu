@@ -923,97 +923,137 @@ qv_status get_kernels(qv_state *s, const std::vector<std::string> &srcs, const c
 
 }  // namespace
 
-qv_status jit_run_plan(qv_state *s, const std::vector<plan::Pass> &passes)
+struct JitProgram {
+    std::vector<std::shared_ptr<Compiled>> fns;
+    std::vector<std::vector<uint64_t>> args;  // by-value kernel parameter of each pass
+    std::vector<int> threads;
+    std::vector<uint64_t> ntiles;
+};
+
+qv_status jit_prepare(qv_state *s, const std::vector<plan::Pass> &passes, std::shared_ptr<JitProgram> &out)
 {
     const bool c64 = s->dt == QV_C64;
+    auto P = std::make_shared<JitProgram>();
     std::vector<std::string> srcs(passes.size());
     std::vector<size_t> smem(passes.size());
-    std::vector<int> threads(passes.size());
+    P->threads.resize(passes.size());
     for (size_t i = 0; i < passes.size(); ++i) {
         srcs[i] = gen_source(passes[i], c64);
         smem[i] = (c64 ? 8 : 16) * (size_t(1) << passes[i].k);
-        threads[i] = 1 << (passes[i].k - kRegBits);
+        P->threads[i] = 1 << (passes[i].k - kRegBits);
+        P->ntiles.push_back(dim(s) >> passes[i].k);
     }
-    std::vector<std::shared_ptr<Compiled>> fns;
-    QV_TRY(get_kernels(s, srcs, "qv_pass", smem, threads, fns));
-    // launch every pass with its coefficients as a by-value parameter
-    std::vector<uint64_t> coef;
-    for (size_t i = 0; i < passes.size(); ++i) {
-        const plan::Pass &p = passes[i];
+    QV_TRY(get_kernels(s, srcs, "qv_pass", smem, P->threads, P->fns));
+    for (const plan::Pass &p : passes) {
         size_t total = 0;
         for (const plan::Op &op : p.ops) total += c64 ? size_t(coef_slots_c64(op)) : 16;
-        coef.assign(std::max<size_t>(1, total), 0);
+        std::vector<uint64_t> coef(std::max<size_t>(1, total), 0);
         size_t off = 0;
         for (const plan::Op &op : p.ops) {
             if (c64) op_coeffs_c64(op, coef.data() + off);
             else op_coeffs_c128(op, reinterpret_cast<double *>(coef.data() + off));
             off += c64 ? size_t(coef_slots_c64(op)) : 16;
         }
-        const Compiled &c = *fns[i];
-        const uint64_t ntiles = dim(s) >> p.k;
+        P->args.push_back(std::move(coef));
+    }
+    out = P;
+    return QV_OK;
+}
+
+qv_status jit_launch(qv_state *s, const JitProgram &P)
+{
+    QV_CUDA(cudaSetDevice(s->device));
+    for (size_t i = 0; i < P.fns.size(); ++i) {
+        const Compiled &c = *P.fns[i];
+        uint64_t ntiles = P.ntiles[i];
         const unsigned grid = unsigned(std::min<uint64_t>(ntiles, uint64_t(c.per_sm) * s->num_sms));
         void *amp = s->amp;
-        void *args[] = {&amp, const_cast<uint64_t *>(&ntiles), coef.data()};
+        void *args[] = {&amp, &ntiles, const_cast<uint64_t *>(P.args[i].data())};
         prof_bytes(s, QV_K_FUSED, 2.0 * double(dim(s)) * amp_bytes(s->dt));
         prof_begin(s, QV_K_FUSED);
-        const CUresult r = api().launch(c.fn, grid, 1, 1, unsigned(threads[i]), 1, 1, unsigned(c.smem),
+        const CUresult r = api().launch(c.fn, grid, 1, 1, unsigned(P.threads[i]), 1, 1, unsigned(c.smem),
                                           reinterpret_cast<CUstream>(s->stream), args, nullptr);
         prof_end(s, QV_K_FUSED);
         if (r != CUDA_SUCCESS) return cu_fail(r, "cuLaunchKernel");
-        s->prof.h2d += coef.size() * sizeof(uint64_t);
+        s->prof.h2d += P.args[i].size() * sizeof(uint64_t);
     }
     return QV_OK;
 }
 
-qv_status jit_run_adjoint(qv_state *s, const std::vector<plan::Pass> &passes, void *lam, double *part, int G)
+qv_status jit_run_plan(qv_state *s, const std::vector<plan::Pass> &passes)
+{
+    std::shared_ptr<JitProgram> P;
+    QV_TRY(jit_prepare(s, passes, P));
+    return jit_launch(s, *P);
+}
+
+qv_status jit_prepare_adjoint(qv_state *s, const std::vector<plan::Pass> &passes, std::shared_ptr<JitProgram> &out)
 {
     if (s->dt != QV_C64) return fail(QV_ERR_UNSUPPORTED, "compiled adjoint passes are complex64 only");
+    auto P = std::make_shared<JitProgram>();
     std::vector<std::string> srcs(passes.size());
     std::vector<size_t> smem(passes.size());
-    std::vector<int> threads(passes.size()), nslots(passes.size(), 0);
+    std::vector<int> nslots(passes.size(), 0);
+    P->threads.resize(passes.size());
     for (size_t i = 0; i < passes.size(); ++i) {
         for (const plan::Op &op : passes[i].ops) nslots[i] += op.nd;
         srcs[i] = gen_source_adj(passes[i], nslots[i]);
-        threads[i] = 1 << (passes[i].k - kRegBits);
-        smem[i] = 8 * (size_t(1) << passes[i].k) + size_t(2 * sizeof(float)) * nslots[i] * (threads[i] / 32);
+        P->threads[i] = 1 << (passes[i].k - kRegBits);
+        smem[i] = 8 * (size_t(1) << passes[i].k) + size_t(2 * sizeof(float)) * nslots[i] * (P->threads[i] / 32);
+        P->ntiles.push_back(dim(s) >> passes[i].k);
     }
-    std::vector<std::shared_ptr<Compiled>> fns;
-    QV_TRY(get_kernels(s, srcs, "qv_adj", smem, threads, fns));
-    std::vector<uint64_t> args_buf;
+    QV_TRY(get_kernels(s, srcs, "qv_adj", smem, P->threads, P->fns));
     for (size_t i = 0; i < passes.size(); ++i) {
         const plan::Pass &p = passes[i];
         size_t total = 0;
         for (const plan::Op &op : p.ops) total += size_t(coef_slots_adj(op));
         total = std::max<size_t>(1, total);
         const size_t ns = std::max(1, nslots[i]);
-        args_buf.assign(total + (ns + 1) / 2, 0);  // QvAdjArgs: u64 c[total]; int gslot[ns]
+        std::vector<uint64_t> buf(total + (ns + 1) / 2, 0);  // QvAdjArgs: u64 c[total]; int gslot[ns]
         size_t off = 0;
-        int32_t *gslot = reinterpret_cast<int32_t *>(args_buf.data() + total);
+        int32_t *gslot = reinterpret_cast<int32_t *>(buf.data() + total);
         int lsl = 0;
         for (const plan::Op &op : p.ops) {
-            op_coeffs_c64(op, args_buf.data() + off);
+            op_coeffs_c64(op, buf.data() + off);
             for (int d = 0; d < op.nd; ++d) {
                 for (int e = 0; e < 4; ++e)
-                    lane_triple(args_buf.data() + off + 24 + 12 * d + 3 * e, op.sreg == 3 ? cd(0.0) : op.D[d][e],
+                    lane_triple(buf.data() + off + 24 + 12 * d + 3 * e, op.sreg == 3 ? cd(0.0) : op.D[d][e],
                                 op.D[d][e]);
                 gslot[lsl++] = op.slot + d;
             }
             off += size_t(coef_slots_adj(op));
         }
-        const Compiled &c = *fns[i];
-        const uint64_t ntiles = dim(s) >> p.k;
+        P->args.push_back(std::move(buf));
+    }
+    out = P;
+    return QV_OK;
+}
+
+qv_status jit_launch_adjoint(qv_state *s, const JitProgram &P, void *lam, double *part, int G)
+{
+    QV_CUDA(cudaSetDevice(s->device));
+    for (size_t i = 0; i < P.fns.size(); ++i) {
+        const Compiled &c = *P.fns[i];
+        uint64_t ntiles = P.ntiles[i];
         const unsigned grid = unsigned(std::min<uint64_t>({ntiles, uint64_t(c.per_sm) * s->num_sms, uint64_t(G)}));
         void *amp = s->amp;
-        void *args[] = {&amp, &lam, const_cast<uint64_t *>(&ntiles), &part, &G, args_buf.data()};
+        void *args[] = {&amp, &lam, &ntiles, &part, &G, const_cast<uint64_t *>(P.args[i].data())};
         prof_bytes(s, QV_K_ADJOINT, 4.0 * double(dim(s)) * amp_bytes(s->dt));
         prof_begin(s, QV_K_ADJOINT);
-        const CUresult r = api().launch(c.fn, grid, 1, 1, unsigned(threads[i]), 1, 1, unsigned(c.smem),
+        const CUresult r = api().launch(c.fn, grid, 1, 1, unsigned(P.threads[i]), 1, 1, unsigned(c.smem),
                                           reinterpret_cast<CUstream>(s->stream), args, nullptr);
         prof_end(s, QV_K_ADJOINT);
         if (r != CUDA_SUCCESS) return cu_fail(r, "cuLaunchKernel");
-        s->prof.h2d += args_buf.size() * sizeof(uint64_t);
+        s->prof.h2d += P.args[i].size() * sizeof(uint64_t);
     }
     return QV_OK;
+}
+
+qv_status jit_run_adjoint(qv_state *s, const std::vector<plan::Pass> &passes, void *lam, double *part, int G)
+{
+    std::shared_ptr<JitProgram> P;
+    QV_TRY(jit_prepare_adjoint(s, passes, P));
+    return jit_launch_adjoint(s, *P, lam, part, G);
 }
 
 }  // namespace qv
