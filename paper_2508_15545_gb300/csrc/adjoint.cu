@@ -46,7 +46,11 @@ constexpr int kMaxTerms = 64;
 // state, and FP64 runs at a small fraction of the FP32 rate on this GPU).
 template <typename R> struct PauliGroupA {
     uint64_t x;
-    int64_t nt;
+    int32_t nt;
+    int32_t zero_z;       // every z mask is 0: c is the constant (c0re, c0im)
+    int32_t has_im;       // some coefficient has an imaginary part
+    int32_t pad;
+    R c0re, c0im;
     uint64_t z[kMaxTerms];
     R cre[kMaxTerms], cim[kMaxTerms];
 };
@@ -66,11 +70,12 @@ __global__ void __launch_bounds__(kThreads) pauli_apply_kernel(const R *__restri
         R ar = 0, ai = 0;
         for (int q = 0; q < ng; ++q) {
             const uint64_t src = j ^ g[q].x;
-            R cr = 0, ci = 0;
-            for (int k = 0; k < int(g[q].nt); ++k) {
-                const bool neg = __popcll(src & g[q].z[k]) & 1;
-                cr += neg ? -g[q].cre[k] : g[q].cre[k];
-                ci += neg ? -g[q].cim[k] : g[q].cim[k];
+            R cr, ci;
+            if (g[q].zero_z) {
+                cr = g[q].c0re;
+                ci = g[q].c0im;
+            } else {
+                zsign_sum<R>(src, g[q].z, g[q].cre, g[q].cim, g[q].nt, g[q].has_im != 0, cr, ci);
             }
             const R vr = psi[2 * src], vi = psi[2 * src + 1];
             ar += cr * vr - ci * vi;
@@ -281,6 +286,19 @@ qv_status pauli_apply_impl(qv_state *s, const void *src, void *dst, const qv_pau
         g->cre[g->nt] = R(terms[k].coeff * pr[ny & 3]);
         g->cim[g->nt] = R(terms[k].coeff * pi[ny & 3]);
         g->nt++;
+    }
+    for (PauliGroupA<R> &gg : groups) {
+        gg.zero_z = 1;
+        gg.has_im = 0;
+        double c0r = 0, c0i = 0;
+        for (int k = 0; k < gg.nt; ++k) {
+            gg.zero_z &= gg.z[k] == 0;
+            gg.has_im |= gg.cim[k] != R(0);
+            c0r += double(gg.cre[k]);
+            c0i += double(gg.cim[k]);
+        }
+        gg.c0re = R(c0r);
+        gg.c0im = R(c0i);
     }
     const size_t gbytes = groups.size() * sizeof(PauliGroupA<R>);
     if (gbytes > 200 * 1024) return fail(QV_ERR_UNSUPPORTED, "Hamiltonian too large (%zu X-mask groups)", groups.size());

@@ -133,6 +133,11 @@ constexpr int kMaxGroupTerms = 64;
 struct BGroup {
     uint64_t x;
     int nt;
+    int zero_z;   // every z mask is 0: c(i) is the constant (c0re, c0im)
+    int has_im;   // some coefficient has an imaginary part
+    int pad;
+    double c0re, c0im;
+    float f0re, f0im;
     uint64_t z[kMaxGroupTerms];
     double cre[kMaxGroupTerms], cim[kMaxGroupTerms];
     float fre[kMaxGroupTerms], fim[kMaxGroupTerms];  // the same in FP32, for complex64 states
@@ -161,19 +166,19 @@ __global__ void __launch_bounds__(kBThreads) batch_pauli_kernel(R *const *amps, 
             const uint64_t j = i ^ g[q].x;
             const R br = a[2 * j], bi = a[2 * j + 1];
             const R pr = br * ar + bi * ai, pi = br * ai - bi * ar;  // conj(b) a
-            R cr = 0, ci = 0;
-            for (int k = 0; k < g[q].nt; ++k) {
-                const bool neg = __popcll(i & g[q].z[k]) & 1;
-                R ur, ui;
+            R cr, ci;
+            if (g[q].zero_z) {
                 if constexpr (sizeof(R) == 4) {
-                    ur = g[q].fre[k];
-                    ui = g[q].fim[k];
+                    cr = g[q].f0re;
+                    ci = g[q].f0im;
                 } else {
-                    ur = g[q].cre[k];
-                    ui = g[q].cim[k];
+                    cr = g[q].c0re;
+                    ci = g[q].c0im;
                 }
-                cr += neg ? -ur : ur;
-                ci += neg ? -ui : ui;
+            } else if constexpr (sizeof(R) == 4) {
+                zsign_sum<R>(i, g[q].z, g[q].fre, g[q].fim, g[q].nt, g[q].has_im != 0, cr, ci);
+            } else {
+                zsign_sum<R>(i, g[q].z, g[q].cre, g[q].cim, g[q].nt, g[q].has_im != 0, cr, ci);
             }
             acc.add(pr * cr - pi * ci);
         }
@@ -423,6 +428,18 @@ qv_status build(qv_batch *b, const qv_batch_item *items, size_t count, const qv_
             g->fre[g->nt] = float(g->cre[g->nt]);
             g->fim[g->nt] = float(g->cim[g->nt]);
             g->nt++;
+            g->c0re += g->cre[g->nt - 1];
+            g->c0im += g->cim[g->nt - 1];
+            g->f0re = float(g->c0re);
+            g->f0im = float(g->c0im);
+        }
+        for (BGroup &gg : hg) {
+            gg.zero_z = 1;
+            gg.has_im = 0;
+            for (int k = 0; k < gg.nt; ++k) {
+                gg.zero_z &= gg.z[k] == 0;
+                gg.has_im |= gg.cim[k] != 0.0;
+            }
         }
         if (hg.size() * sizeof(BGroup) > 200 * 1024) return fail(QV_ERR_UNSUPPORTED, "Hamiltonian too large");
         b->nhgroups = int(hg.size());

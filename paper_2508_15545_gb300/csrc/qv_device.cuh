@@ -31,6 +31,27 @@ __device__ __forceinline__ bool wait_counter(const unsigned *ctr, unsigned need,
     return true;
 }
 
+// c(i) = sum_k c_k (-1)^{popcount(i & z_k)} over the nt terms of one X-mask
+// group (Pauli strings: coefficients c_k already carry the i^{#Y} factor).
+// Parities from 32-bit popcounts of the two halves of the index; the
+// imaginary part is skipped for groups whose coefficients are all real.
+template <typename R>
+__device__ __forceinline__ void zsign_sum(uint64_t i, const uint64_t *z, const R *cre, const R *cim, int nt,
+                                          bool has_im, R &cr, R &ci)
+{
+    const uint32_t lo = uint32_t(i), hi = uint32_t(i >> 32);
+    cr = R(0);
+    ci = R(0);
+#pragma unroll 4
+    for (int k = 0; k < nt; ++k) {
+        const uint64_t zk = z[k];
+        const uint32_t par = (__popc(lo & uint32_t(zk)) ^ __popc(hi & uint32_t(zk >> 32))) & 1u;
+        const R sg = par ? R(-1) : R(1);
+        cr += sg * cre[k];
+        if (has_im) ci += sg * cim[k];
+    }
+}
+
 // Insert a 0 at bit position b of x (bits >= b move up by one).
 __host__ __device__ __forceinline__ uint64_t insert_zero(uint64_t x, int b)
 {

@@ -178,12 +178,8 @@ __global__ void __launch_bounds__(kThreads) pauli_kernel(const R *__restrict__ a
         const R br = amp[2 * j], bi = amp[2 * j + 1];
         // conj(b) a
         const R pr = br * ar + bi * ai, pi = br * ai - bi * ar;
-        R cr = 0, ci = 0;
-        for (int k = 0; k < sg.nt; ++k) {
-            const bool neg = __popcll(i & sg.z[k]) & 1;
-            cr += neg ? -cre[k] : cre[k];
-            ci += neg ? -cim[k] : cim[k];
-        }
+        R cr, ci;
+        zsign_sum<R>(i, sg.z, cre, cim, sg.nt, true, cr, ci);
         acc.add(pr * cr - pi * ci);
     }
     double x[1] = {acc.value()};
