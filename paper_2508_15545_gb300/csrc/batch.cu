@@ -16,6 +16,7 @@
 
 #include "fused_device.cuh"
 #include "qv_internal.h"
+#include "qv_jit.h"
 #include "qv_plan.h"
 
 namespace qv {
@@ -234,6 +235,12 @@ struct BatchGroup {
     uint32_t nitems = 0, npasses = 0;
     size_t smem = 0;
     unsigned grid = 0;
+    // compiled path: every circuit of the group has the same plan structure
+    bool jit = false;
+    JitBatch jb;
+    void *jamps = nullptr, *jcoefs = nullptr;
+    uint64_t ntiles = 0;
+    uint32_t nchunks = 0;
 };
 
 }  // namespace qv
@@ -290,6 +297,15 @@ template <typename R> qv_status group_occupancy(int K, size_t smem, int *per_sm)
 template <typename R>
 void launch_group(qv_batch *b, const BatchGroup &g, unsigned *next)
 {
+    if (g.jit) {
+        uint32_t nitems = g.nitems, nchunks = g.nchunks, spin = kSpinLimit;
+        uint64_t ntiles = g.ntiles;
+        void *amps = g.jamps, *coefs = g.jcoefs, *items = g.items, *done = g.done, *st = b->status;
+        void *nx = next;
+        void *args[] = {&amps, &coefs, &items, &nitems, &nx, &done, &st, &ntiles, &nchunks, &spin};
+        jit_launch_batch(g.jb, b->stream, g.grid, args);  // a failure shows in cudaGetLastError / the capture
+        return;
+    }
     R *const *amps = static_cast<R *const *>(b->amps);
     auto args = [&](auto kern) {
         kern<<<g.grid, 1 << (g.K - kRegBits), g.smem, b->stream>>>(
@@ -350,10 +366,46 @@ qv_status build(qv_batch *b, const qv_batch_item *items, size_t count, const qv_
     QV_TRY(dmalloc(b, &st, sizeof(int)));
     b->status = static_cast<int *>(st);
     // ---- one persistent launch per tile size
+    const bool jit_ok = sizeof(R) == 4 && jit_available(nullptr) && !(opts && (opts->flags & QV_PLAN_INTERPRET));
     for (auto &kv : by_k) {
         BatchGroup g;
         g.K = kv.first;
         g.circuits = kv.second;
+        bool same = jit_ok;
+        for (int c : g.circuits)
+            same = same && nq[c] == nq[g.circuits[0]] && jit_same_structure(plans[c], plans[g.circuits[0]]);
+        if (same) {  // compiled persistent kernel over (circuit, pass, chunk) items
+            g.jit = true;
+            std::vector<std::vector<plan::Pass> *> pl;
+            std::vector<void *> ga;
+            for (int c : g.circuits) {
+                pl.push_back(&plans[c]);
+                ga.push_back(amps[c]);
+            }
+            QV_TRY(jit_prepare_batch(items[g.circuits[0]].state, pl, int(kChunkTiles), g.jb));
+            const uint32_t np = uint32_t(g.jb.npasses);
+            g.ntiles = uint64_t(1) << (nq[g.circuits[0]] - g.K);
+            g.nchunks = uint32_t((g.ntiles + kChunkTiles - 1) / kChunkTiles);
+            std::vector<uint2> it;
+            for (uint32_t r = 0; r < np; ++r)
+                for (uint32_t cl = 0; cl < uint32_t(g.circuits.size()); ++cl)
+                    for (uint32_t k = 0; k < g.nchunks; ++k) it.push_back(make_uint2(cl * np + r, k));
+            g.nitems = uint32_t(it.size());
+            g.npasses = uint32_t(g.circuits.size()) * np;
+            QV_TRY(dmalloc(b, &g.jamps, ga.size() * sizeof(void *)));
+            QV_TRY(dmalloc(b, &g.jcoefs, g.jb.coefs.size() * sizeof(uint64_t)));
+            QV_TRY(dmalloc(b, &g.items, it.size() * sizeof(uint2)));
+            QV_TRY(dmalloc(b, &g.done, g.npasses * sizeof(unsigned)));
+            QV_CUDA(cudaMemcpy(g.jamps, ga.data(), ga.size() * sizeof(void *), cudaMemcpyHostToDevice));
+            QV_CUDA(cudaMemcpy(g.jcoefs, g.jb.coefs.data(), g.jb.coefs.size() * sizeof(uint64_t),
+                               cudaMemcpyHostToDevice));
+            QV_CUDA(cudaMemcpy(g.items, it.data(), it.size() * sizeof(uint2), cudaMemcpyHostToDevice));
+            g.jb.coefs.clear();
+            g.jb.coefs.shrink_to_fit();
+            g.grid = unsigned(g.jb.per_sm) * b->num_sms;
+            b->groups.push_back(g);
+            continue;
+        }
         // larger circuits first within a round
         std::stable_sort(g.circuits.begin(), g.circuits.end(),
                          [&](int a, int c) { return nq[a] > nq[c]; });

@@ -464,24 +464,11 @@ void emit_op_c128(std::ostream &o, const plan::Op &op, int k)
 // K = 10 5 % faster at 12 than at 8; K = 12 is fastest at 3.
 int min_blocks(bool c64, int k) { return k == 12 ? (c64 ? 3 : 1) : k == 11 ? (c64 ? 6 : 2) : (c64 ? 12 : 2); }
 
-std::string gen_source(const plan::Pass &p, bool c64)
+// Thread-invariant offsets of a pass: global offsets of the load and store
+// layouts and the shared-memory word offsets of every transpose.
+void emit_pass_consts(std::ostream &o, const plan::Pass &p, bool c64)
 {
     PassGeom G{p.k, p.k - kRegBits, p.k - kChunkBits, &p};
-    const int T = 1 << G.nq;
-    const int nops = int(p.ops.size());
-    std::vector<int> coff(nops + 1, 0);  // coefficient offset of each op
-    for (int k = 0; k < nops; ++k) coff[k + 1] = coff[k] + (c64 ? coef_slots_c64(p.ops[k]) : 16);
-    const int ncoef = std::max(1, coff[nops]);
-    const int nreg = c64 ? 3 : 4;  // register bits addressed per vector/slot (c64: bit 3 is the lane)
-    const int nvec = 1 << nreg;
-    std::ostringstream o;
-    o << kPrelude;
-    o << "struct QvCoef { " << (c64 ? "u64" : "double") << " c[" << ncoef << "]; };\n";
-    o << "extern \"C\" __global__ void __launch_bounds__(" << T << ", " << min_blocks(c64, p.k) << ") qv_pass("
-      << (c64 ? "float" : "double") << " *__restrict__ amp, u64 ntiles, const QvCoef cf)\n{\n";
-    o << "    extern __shared__ __align__(16) u64 sm[];\n";
-    o << "    const u32 tid = threadIdx.x;\n";
-    // loop-invariant thread offsets
     auto phys_mask = [&](const int8_t *Q) {
         std::vector<uint64_t> m(G.nq);
         for (int b = 0; b < G.nq; ++b) m[b] = G.phys(1u << Q[b]);
@@ -499,7 +486,22 @@ std::string gen_source(const plan::Pass &p, bool c64)
         o << "    const u32 wW" << s << " = " << thread_expr(word_mask(p.stages[s - 1].out.Q), false) << ";\n";
         o << "    const u32 wR" << s << " = " << thread_expr(word_mask(p.stages[s].in.Q), false) << ";\n";
     }
-    o << "    for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {\n";
+}
+
+// One tile of a pass (tile index t): base index, load, stages with their
+// transposes and ops, store. Coefficients are read as cf.c[...]; with
+// l2_loads the tile is read through L2 only (other CTAs may have written it
+// since this SM last cached it).
+void emit_tile_body(std::ostream &o, const plan::Pass &p, bool c64, bool l2_loads)
+{
+    PassGeom G{p.k, p.k - kRegBits, p.k - kChunkBits, &p};
+    const int nops = int(p.ops.size());
+    std::vector<int> coff(nops + 1, 0);  // coefficient offset of each op
+    for (int k = 0; k < nops; ++k) coff[k + 1] = coff[k] + (c64 ? coef_slots_c64(p.ops[k]) : 16);
+    const int nreg = c64 ? 3 : 4;  // register bits addressed per vector/slot (c64: bit 3 is the lane)
+    const int nvec = 1 << nreg;
+    const plan::Stage &s0 = p.stages.front(), &sl = p.stages.back();
+    const std::string ld0 = l2_loads ? "__ldcg(" : "*", ld1 = l2_loads ? ")" : "";
     o << "    const u64 base = 0ull";
     for (int s = 0; s < p.nseg; ++s)
         o << " | (((t >> " << p.seg_src[s] << ") & " << hex64((uint64_t(1) << p.seg_w[s]) - 1) << ") << "
@@ -515,8 +517,8 @@ std::string gen_source(const plan::Pass &p, bool c64)
         o << "    u64 r[8], i[8];\n";
         o << "    { const float *a = amp + 2 * (base + gL);\n";
         for (int v = 0; v < 8; ++v)
-            o << "      const float4 f" << v << " = *reinterpret_cast<const float4 *>(a + 2 * "
-              << hex64(G.phys(reg_offset(s0.in.P, v))) << ");\n";
+            o << "      const float4 f" << v << " = " << ld0 << "reinterpret_cast<const float4 *>(a + 2 * "
+              << hex64(G.phys(reg_offset(s0.in.P, v))) << ")" << ld1 << ";\n";
         for (int v = 0; v < 8; ++v)
             o << "      r[" << v << "] = pk(f" << v << ".x, f" << v << ".z); i[" << v << "] = pk(f" << v << ".y, f" << v
               << ".w);\n";
@@ -525,7 +527,8 @@ std::string gen_source(const plan::Pass &p, bool c64)
         o << "    double r[16], i[16];\n";
         o << "    { const double2 *a = reinterpret_cast<const double2 *>(amp) + (base + gL);\n";
         for (int m = 0; m < 16; ++m)
-            o << "      const double2 f" << m << " = a[" << hex64(G.phys(reg_offset(s0.in.P, m))) << "];\n";
+            o << "      const double2 f" << m << " = " << ld0 << "(a + " << hex64(G.phys(reg_offset(s0.in.P, m))) << ")"
+              << ld1 << ";\n";
         for (int m = 0; m < 16; ++m) o << "      r[" << m << "] = f" << m << ".x; i[" << m << "] = f" << m << ".y;\n";
         o << "    }\n";
     }
@@ -580,6 +583,105 @@ std::string gen_source(const plan::Pass &p, bool c64)
               << "]);\n";
         o << "    }\n";
     }
+}
+
+std::string gen_source(const plan::Pass &p, bool c64)
+{
+    PassGeom G{p.k, p.k - kRegBits, p.k - kChunkBits, &p};
+    const int T = 1 << G.nq;
+    const int nops = int(p.ops.size());
+    int ncoef = 0;
+    for (int k = 0; k < nops; ++k) ncoef += c64 ? coef_slots_c64(p.ops[k]) : 16;
+    ncoef = std::max(1, ncoef);
+    std::ostringstream o;
+    o << kPrelude;
+    o << "struct QvCoef { " << (c64 ? "u64" : "double") << " c[" << ncoef << "]; };\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(" << T << ", " << min_blocks(c64, p.k) << ") qv_pass("
+      << (c64 ? "float" : "double") << " *__restrict__ amp, u64 ntiles, const QvCoef cf)\n{\n";
+    o << "    extern __shared__ __align__(16) u64 sm[];\n";
+    o << "    const u32 tid = threadIdx.x;\n";
+    emit_pass_consts(o, p, c64);
+    o << "    for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {\n";
+    emit_tile_body(o, p, c64, false);
+    o << "    }\n}\n";
+    return o.str();
+}
+
+// ---------------------------------------------------------------- batched passes (complex64)
+// Many circuits that share one plan structure (same passes, layouts and op
+// kinds; only the coefficients differ), as one persistent kernel: CTAs claim
+// work items (circuit, pass, chunk of tiles) from a counter, wait (bounded)
+// until the previous pass of that circuit is complete, and run the pass's
+// compiled tile code with that circuit's coefficients from global memory.
+
+bool same_structure(const plan::Pass &a, const plan::Pass &b)
+{
+    if (a.k != b.k || a.nseg != b.nseg || a.stages.size() != b.stages.size() || a.ops.size() != b.ops.size())
+        return false;
+    for (int j = 0; j < a.k - kChunkBits; ++j)
+        if (a.s_high[j] != b.s_high[j]) return false;
+    for (int q = 0; q < a.nseg; ++q)
+        if (a.seg_src[q] != b.seg_src[q] || a.seg_w[q] != b.seg_w[q] || a.seg_dst[q] != b.seg_dst[q]) return false;
+    for (size_t s = 0; s < a.stages.size(); ++s)
+        if (std::memcmp(&a.stages[s], &b.stages[s], sizeof(plan::Stage)) != 0) return false;
+    for (size_t k = 0; k < a.ops.size(); ++k) {
+        const plan::Op &x = a.ops[k], &y = b.ops[k];
+        if (x.type != y.type || x.treg != y.treg || x.treg2 != y.treg2 || x.sreg != y.sreg || x.m0id != y.m0id ||
+            x.sthr != y.sthr || x.tthr != y.tthr || x.sext != y.sext || x.text != y.text || x.nd != y.nd)
+            return false;
+    }
+    return true;
+}
+
+std::string gen_source_batch(const std::vector<plan::Pass> &passes, int stride, int chunk_tiles)
+{
+    const int k = passes.front().k;
+    const int T = 1 << (k - kRegBits);
+    const int np = int(passes.size());
+    std::ostringstream o;
+    o << kPrelude;
+    o << "QI u32 ld_acq(const unsigned *p) { u32 v; asm volatile(\"ld.acquire.gpu.global.u32 %0, [%1];\" : \"=r\"(v) : \"l\"(p) : \"memory\"); return v; }\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(" << T << ", " << min_blocks(true, k)
+      << ") qv_batch(float *const *amps, const u64 *__restrict__ coefs, const uint2 *__restrict__ items, u32 nitems, "
+         "unsigned *next, unsigned *done, int *status, u64 ntiles, u32 nchunks, u32 spin_limit)\n{\n";
+    o << "    extern __shared__ __align__(16) u64 sm[];\n";
+    o << "    __shared__ u32 s_item; __shared__ int s_abort;\n";
+    o << "    const u32 tid = threadIdx.x;\n";
+    o << "    for (;;) {\n";
+    o << "    if (tid == 0) { s_item = atomicAdd(next, 1u); s_abort = 0; }\n";
+    o << "    __syncthreads();\n";
+    o << "    const u32 item = s_item;\n";
+    o << "    if (item >= nitems) break;\n";
+    o << "    const uint2 it = items[item];  // x = circuit * passes + pass, y = chunk\n";
+    o << "    const u32 pass = it.x % " << np << "u, circ = it.x / " << np << "u;\n";
+    o << "    if (tid == 0 && pass > 0) {  // bounded wait for the previous pass of this circuit\n";
+    o << "        u32 spins = 0;\n";
+    o << "        while (ld_acq(&done[it.x - 1]) < nchunks) {\n";
+    o << "            if (++spins > spin_limit || *reinterpret_cast<volatile int *>(status) != 0) {\n";
+    o << "                atomicCAS(status, 0, 4); s_abort = 1; break; }\n";
+    o << "            __nanosleep(128);\n";
+    o << "        }\n";
+    o << "    }\n";
+    o << "    __syncthreads();\n";
+    o << "    if (s_abort) break;\n";
+    o << "    float *amp = amps[circ];\n";
+    o << "    const u64 *cf = coefs + (size_t)it.x * " << stride << "u;\n";
+    o << "    const u64 t0 = (u64)it.y * " << chunk_tiles << "u, t1 = min(ntiles, t0 + " << chunk_tiles << "u);\n";
+    o << "    switch (pass) {\n";
+    for (int p = 0; p < np; ++p) {
+        o << "    case " << p << ": {\n";
+        emit_pass_consts(o, passes[p], true);
+        o << "    for (u64 t = t0; t < t1; ++t) {\n";
+        std::ostringstream body;
+        emit_tile_body(body, passes[p], true, true);
+        std::string bs = body.str();
+        for (size_t q = bs.find("cf.c["); q != std::string::npos; q = bs.find("cf.c[", q)) bs.replace(q, 5, "cf[");
+        o << bs;
+        o << "    }\n    } break;\n";
+    }
+    o << "    default: break;\n    }\n";
+    o << "    __syncthreads();\n";
+    o << "    if (tid == 0) { __threadfence(); atomicAdd(&done[it.x], 1u); }\n";
     o << "    }\n}\n";
     return o.str();
 }
@@ -797,6 +899,8 @@ std::string gen_source_adj(const plan::Pass &p, int nslots)
     return o.str();
 }
 
+}  // namespace
+
 // ---------------------------------------------------------------- compile + cache
 struct Compiled {
     CUmodule mod = nullptr;
@@ -804,6 +908,8 @@ struct Compiled {
     int per_sm = 0;
     size_t smem = 0;
 };
+
+namespace {
 
 std::mutex g_cache_mu;
 std::map<std::pair<int, std::string>, std::shared_ptr<Compiled>> g_cache;
@@ -1054,6 +1160,53 @@ qv_status jit_run_adjoint(qv_state *s, const std::vector<plan::Pass> &passes, vo
     std::shared_ptr<JitProgram> P;
     QV_TRY(jit_prepare_adjoint(s, passes, P));
     return jit_launch_adjoint(s, *P, lam, part, G);
+}
+
+qv_status jit_prepare_batch(qv_state *s, const std::vector<std::vector<plan::Pass> *> &plans, int chunk_tiles,
+                            JitBatch &out)
+{
+    const std::vector<plan::Pass> &P0 = *plans.front();
+    out.npasses = int(P0.size());
+    out.stride = 1;
+    for (const plan::Pass &p : P0) {
+        int t = 0;
+        for (const plan::Op &op : p.ops) t += coef_slots_c64(op);
+        out.stride = std::max(out.stride, t);
+    }
+    out.coefs.assign(plans.size() * P0.size() * size_t(out.stride), 0);
+    for (size_t c = 0; c < plans.size(); ++c)
+        for (size_t p = 0; p < P0.size(); ++p) {
+            uint64_t *dst = out.coefs.data() + (c * P0.size() + p) * size_t(out.stride);
+            size_t off = 0;
+            for (const plan::Op &op : (*plans[c])[p].ops) {
+                op_coeffs_c64(op, dst + off);
+                off += size_t(coef_slots_c64(op));
+            }
+        }
+    const std::string src = gen_source_batch(P0, out.stride, chunk_tiles);
+    out.threads = 1 << (P0.front().k - kRegBits);
+    out.smem = 8 * (size_t(1) << P0.front().k);
+    std::vector<std::shared_ptr<Compiled>> fns;
+    QV_TRY(get_kernels(s, {src}, "qv_batch", {out.smem}, {out.threads}, fns));
+    out.fn = fns[0];
+    out.per_sm = fns[0]->per_sm;
+    return QV_OK;
+}
+
+qv_status jit_launch_batch(const JitBatch &jb, cudaStream_t stream, unsigned grid, void **args)
+{
+    const CUresult r = api().launch(jb.fn->fn, grid, 1, 1, unsigned(jb.threads), 1, 1, unsigned(jb.smem),
+                                    reinterpret_cast<CUstream>(stream), args, nullptr);
+    if (r != CUDA_SUCCESS) return cu_fail(r, "cuLaunchKernel");
+    return QV_OK;
+}
+
+bool jit_same_structure(const std::vector<plan::Pass> &a, const std::vector<plan::Pass> &b)
+{
+    if (a.size() != b.size()) return false;
+    for (size_t i = 0; i < a.size(); ++i)
+        if (!same_structure(a[i], b[i])) return false;
+    return true;
 }
 
 }  // namespace qv

@@ -30,4 +30,22 @@ qv_status jit_run_plan(qv_state *s, const std::vector<plan::Pass> &passes);
 // not launched are left untouched.
 qv_status jit_run_adjoint(qv_state *s, const std::vector<plan::Pass> &passes, void *lam, double *part, int G);
 
+// Batched circuits of one plan structure (complex64) in one persistent kernel.
+struct Compiled;
+struct JitBatch {
+    std::shared_ptr<Compiled> fn;
+    std::vector<uint64_t> coefs;  // [circuit][pass][stride]
+    int npasses = 0, stride = 0, threads = 0, per_sm = 0;
+    size_t smem = 0;
+};
+// True when two plans differ at most in their coefficients.
+bool jit_same_structure(const std::vector<plan::Pass> &a, const std::vector<plan::Pass> &b);
+// Compiles the kernel of plans[0]'s structure and packs every plan's coefficients.
+qv_status jit_prepare_batch(qv_state *s, const std::vector<std::vector<plan::Pass> *> &plans, int chunk_tiles,
+                            JitBatch &out);
+// Launches (or records into a capturing stream) the kernel with args:
+// amps, coefs, items (uint2: circuit * passes + pass, chunk), nitems, next,
+// done, status, ntiles, nchunks, spin_limit.
+qv_status jit_launch_batch(const JitBatch &jb, cudaStream_t stream, unsigned grid, void **args);
+
 }  // namespace qv

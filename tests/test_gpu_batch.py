@@ -8,7 +8,9 @@ from paper_2508_15545_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def test_batch_ansatz_energies(qvlib, orc, cuda):
+# flags 0: one plan structure -> compiled persistent kernel; 2: interpreting kernel
+@pytest.mark.parametrize("flags", [0, 2])
+def test_batch_ansatz_energies(qvlib, orc, cuda, flags):
     """Parameter sets of the hardware-efficient ansatz (RY, RZ, CZ ring) with
     H = sum Z Z + 0.5 sum X: <H> per set, two replays of the same graph."""
     qv = qvlib
@@ -16,7 +18,7 @@ def test_batch_ansatz_energies(qvlib, orc, cuda):
     terms = W.ansatz_hamiltonian(n)
     circuits = [W.ansatz_circuit(n, layers, W.config_seed(2, c))[0] for c in range(count)]
     states = [qv.qv_create(n, 0) for _ in range(count)]
-    b = qv.Batch(list(zip(states, circuits)), terms)
+    b = qv.Batch(list(zip(states, circuits)), terms, flags=flags)
     want = np.array([orc.energy(n, g, terms) for g in circuits])
     for rep in range(2):
         got = b.run()
