@@ -189,3 +189,25 @@ def test_adjoint_tiled_zero_angles(qvlib, orc, cuda, dtype):
     for sweep in (2, 3):
         g, e, _, _ = _adjoint(qv, n, dtype, gates, terms, 9, psi0, sweep=sweep)
         assert np.max(np.abs(g - ref)) <= tol, (sweep, g, ref)
+
+
+def test_adjoint_cache_follows_the_angles(qvlib, orc, cuda):
+    """The compiled sweep is kept per handle for the last gate list; new
+    angles (same structure) must give the new gradient."""
+    qv = qvlib
+    n, layers = 12, 3
+    gates, npar = W.ansatz_circuit(n, layers, W.config_seed(3, 7))
+    terms = W.ansatz_hamiltonian(n)
+    rng = W.SplitMix64(99)
+    h = qv.qv_create(n, 0)
+    try:
+        for rep in range(3):
+            params = rng.uniform(npar) * 2 * math.pi if rep else None
+            gl = gates if params is None else W.with_params(gates, params)
+            for _ in range(2):   # the second call reuses the compiled sweep
+                qv.qv_set_basis(h, 0)
+                g, e = qv.qv_adjoint_grad(h, gl, terms, npar)
+                ref = orc.param_shift_grad(n, gl, terms, npar)
+                assert np.max(np.abs(g - ref)) <= 1e-4, rep
+    finally:
+        qv.qv_destroy(h)

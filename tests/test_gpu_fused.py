@@ -158,3 +158,24 @@ def test_pair_ops_fused(qvlib, orc, cuda, n, k, pairs):
     got_np = run_gpu(qv, n, 0, gates, psi=psi, tile_bits=k, flags=qv.QV_PLAN_NO_PAIRS)
     assert dist(got, want) <= TOL[0]
     assert dist(got_np, want) <= TOL[0]
+
+
+def test_plan_cache_follows_the_gate_list(qvlib, orc, cuda):
+    """The handle keeps the last plan and compiled program; a changed angle,
+    gate list, tile size or flag must re-plan, the same list must reuse."""
+    qv = qvlib
+    n = 14
+    g1 = W.random_circuit(n, 6, W.config_seed(0, 11))
+    g2 = W.random_circuit(n, 6, W.config_seed(0, 12))          # same structure, other angles
+    g3 = W.random_gate_list(n, 80, seed=5, ctrl_prob=0.3)      # other structure
+    g1b = list(g1)
+    g1b[7] = g1b[7]._replace(theta=(g1b[7].theta[0] + 1e-3, g1b[7].theta[1], g1b[7].theta[2]))  # one angle moved
+    h = qv.qv_create(n, 0)
+    try:
+        for gates, tb, flags in [(g1, 0, 0), (g1, 0, 0), (g2, 0, 0), (g1, 0, 0), (g1b, 0, 0), (g3, 0, 0),
+                                 (g3, 10, 0), (g3, 10, qv.QV_PLAN_NO_PAIRS), (g1, 11, 0), (g1, 0, 0)]:
+            qv.qv_set_basis(h, 0)
+            qv.qv_apply_circuit(h, gates, mode=2, tile_bits=tb, flags=flags)
+            assert dist(qv.qv_get_state(h), orc.run(n, gates)) <= TOL[0], (tb, flags)
+    finally:
+        qv.qv_destroy(h)
