@@ -7,6 +7,7 @@
 // partial carries about twice the working precision. Partials are combined in
 // FP64 (shuffle trees inside a block, Neumaier-compensated sums across blocks).
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 
 #include "qv_device.cuh"
@@ -187,6 +188,62 @@ __global__ void __launch_bounds__(kThreads) pauli_kernel(const R *__restrict__ a
     if (threadIdx.x == 0) part[blockIdx.x] = x[0];
 }
 
+// All X-mask groups in one pass over the state: part[block] = this block's
+// share of sum_i sum_groups Re( conj(a_{i^x}) c(i) a_i ).
+struct PauliGroupAll {
+    uint64_t x;
+    int nt;
+    int zero_z;   // every z mask is 0: c(i) is the constant (c0re, c0im)
+    int has_im;   // some coefficient has an imaginary part
+    int pad;
+    double c0re, c0im;
+    float f0re, f0im;
+    uint64_t z[kMaxTermsPerGroup];
+    double cre[kMaxTermsPerGroup], cim[kMaxTermsPerGroup];
+    float fre[kMaxTermsPerGroup], fim[kMaxTermsPerGroup];
+};
+constexpr size_t kPauliAllSmem = 200 * 1024;
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) pauli_all_kernel(const R *__restrict__ amp, uint64_t N,
+                                                             const PauliGroupAll *groups, int ng, double *part)
+{
+    __shared__ double smem[kThreads / 32][1];
+    extern __shared__ unsigned char sraw[];
+    PauliGroupAll *g = reinterpret_cast<PauliGroupAll *>(sraw);
+    static_assert(sizeof(PauliGroupAll) % 8 == 0, "copied as 8-byte words");
+    for (int k = threadIdx.x; k < ng * int(sizeof(PauliGroupAll) / 8); k += kThreads)
+        reinterpret_cast<uint64_t *>(g)[k] = reinterpret_cast<const uint64_t *>(groups)[k];
+    __syncthreads();
+    CompSum<R> acc;
+    for (uint64_t i = uint64_t(blockIdx.x) * kThreads + threadIdx.x; i < N; i += uint64_t(gridDim.x) * kThreads) {
+        const R ar = amp[2 * i], ai = amp[2 * i + 1];
+        for (int q = 0; q < ng; ++q) {
+            const uint64_t j = i ^ g[q].x;
+            const R br = amp[2 * j], bi = amp[2 * j + 1];
+            const R pr = br * ar + bi * ai, pi = br * ai - bi * ar;  // conj(b) a
+            R cr, ci;
+            if (g[q].zero_z) {
+                if constexpr (sizeof(R) == 4) {
+                    cr = g[q].f0re;
+                    ci = g[q].f0im;
+                } else {
+                    cr = g[q].c0re;
+                    ci = g[q].c0im;
+                }
+            } else if constexpr (sizeof(R) == 4) {
+                zsign_sum<R>(i, g[q].z, g[q].fre, g[q].fim, g[q].nt, g[q].has_im != 0, cr, ci);
+            } else {
+                zsign_sum<R>(i, g[q].z, g[q].cre, g[q].cim, g[q].nt, g[q].has_im != 0, cr, ci);
+            }
+            acc.add(pr * cr - pi * ci);
+        }
+    }
+    double x[1] = {acc.value()};
+    block_sum<1>(x, smem);
+    if (threadIdx.x == 0) part[blockIdx.x] = x[0];
+}
+
 __global__ void sum_parts_kernel(const double *part, int np, double *out)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -249,6 +306,56 @@ template <typename R> qv_status pauli_impl(qv_state *s, const qv_pauli_term *ter
     }
     const unsigned grid = unsigned(std::min<uint64_t>((dim(s) + kThreads - 1) / kThreads, uint64_t(s->num_sms) * 4));
     const size_t ng = groups.size();
+    if (ng == 0) {
+        *out_host = 0;
+        return QV_OK;
+    }
+    if (ng * sizeof(PauliGroupAll) <= kPauliAllSmem) {
+        // one pass over the state for all groups
+        std::vector<PauliGroupAll> ga(ng);
+        for (size_t q = 0; q < ng; ++q) {
+            PauliGroupAll &a = ga[q];
+            std::memset(&a, 0, sizeof a);
+            a.x = groups[q].x;
+            a.nt = groups[q].nt;
+            a.zero_z = 1;
+            for (int k = 0; k < a.nt; ++k) {
+                a.z[k] = groups[q].z[k];
+                a.cre[k] = groups[q].cre[k];
+                a.cim[k] = groups[q].cim[k];
+                a.fre[k] = float(a.cre[k]);
+                a.fim[k] = float(a.cim[k]);
+                a.c0re += a.cre[k];
+                a.c0im += a.cim[k];
+                a.zero_z &= a.z[k] == 0;
+                a.has_im |= a.cim[k] != 0.0;
+            }
+            a.f0re = float(a.c0re);
+            a.f0im = float(a.c0im);
+        }
+        const size_t gb = ng * sizeof(PauliGroupAll);
+        QV_TRY(ensure_scratch(s, gb + sizeof(double) * (grid + 1)));
+        char *base = static_cast<char *>(s->scratch.ptr);
+        PauliGroupAll *dg = reinterpret_cast<PauliGroupAll *>(base);
+        double *part = reinterpret_cast<double *>(base + gb), *res = part + grid;
+        QV_TRY(copy_h2d(s, dg, ga.data(), gb));
+        static bool attr[2] = {false, false};
+        if (!attr[sizeof(R) == 8]) {
+            QV_CUDA(cudaFuncSetAttribute(pauli_all_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(kPauliAllSmem)));
+            attr[sizeof(R) == 8] = true;
+        }
+        prof_bytes(s, QV_K_PAULI, double(dim(s)) * 2 * sizeof(R) * double(ng + 1));
+        QV_LAUNCH(s, QV_K_PAULI, pauli_all_kernel<R><<<grid, kThreads, gb, s->stream>>>(
+                                      static_cast<const R *>(s->amp), dim(s), dg, int(ng), part));
+        QV_LAUNCH(s, QV_K_PAULI, sum_parts_kernel<<<1, 32, 0, s->stream>>>(part, int(grid), res));
+        QV_TRY(ensure_host_out(s, 1));
+        QV_TRY(copy_d2h(s, s->host_out, res, sizeof(double)));
+        QV_TRY(sync_and_check(s));
+        *out_host = s->host_out[0];
+        return QV_OK;
+    }
+    // more groups than shared memory holds: one pass per group
     const size_t bytes = ng * sizeof(PauliGroup) + sizeof(double) * (ng * grid + ng + 1);
     QV_TRY(ensure_scratch(s, bytes));
     QV_TRY(ensure_host_out(s, ng + 1));
@@ -256,10 +363,6 @@ template <typename R> qv_status pauli_impl(qv_state *s, const qv_pauli_term *ter
     PauliGroup *dg = reinterpret_cast<PauliGroup *>(base);
     double *part = reinterpret_cast<double *>(base + ng * sizeof(PauliGroup));
     double *res = part + ng * grid;
-    if (ng == 0) {
-        *out_host = 0;
-        return QV_OK;
-    }
     QV_TRY(copy_h2d(s, dg, groups.data(), ng * sizeof(PauliGroup)));
     const R *amp = static_cast<const R *>(s->amp);
     for (size_t k = 0; k < ng; ++k) {

@@ -188,3 +188,25 @@ def test_torch_owned_state(qvlib, orc, cuda):
     got = s.tensor.cpu().numpy()
     assert dist(got, orc.run(n, gates)) <= 1e-5
     s.close()
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("nterms", [40, 160])
+def test_expect_pauli_one_pass_and_many_groups(qvlib, orc, cuda, dtype, nterms):
+    """<psi|H|psi> for random Pauli strings (X, Y, Z mixes): with few X-mask
+    groups every group runs in one pass over the state; with more groups than
+    shared memory holds (160 distinct masks), one pass per group."""
+    qv = qvlib
+    n = 11
+    rng = W.SplitMix64(1234 + nterms)
+    u = rng.integers(0, (1 << n) - 1, 2 * nterms)
+    c = rng.uniform(nterms) * 2.0 - 1.0
+    terms = [(float(c[k]), int(u[2 * k]), int(u[2 * k + 1])) for k in range(nterms)]
+    psi = W.random_state(n, 77 + nterms)
+    h = qv.qv_create(n, dtype)
+    qv.qv_set_state(h, psi)
+    got = qv.qv_expect_pauli(h, terms)
+    ref = psi.astype(np.complex64).astype(np.complex128) if dtype == 0 else psi
+    want = orc.expect_terms(ref, terms)
+    assert abs(got - want) <= (2e-5 if dtype == 0 else 1e-11) * sum(abs(t[0]) for t in terms)
+    qv.qv_destroy(h)
