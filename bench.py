@@ -419,6 +419,21 @@ def extras(args, qv, torch, dev, h64, gates):
                                     "note": "U3 passes move 2 x 8 GiB; CNOT passes only the control-1 half"}
     except Exception as e:  # noqa: BLE001
         res["plain_pair_kernel"] = {"error": str(e)}
+    # 1b. the fused step with each tile size (the autotuner's choice space)
+    try:
+        garr = qv.gates_to_c(gates)
+        sweep = {}
+        for tb in (10, 11, 12):
+            if tb > args.n:
+                continue
+
+            def one(tb=tb):
+                qv.qv_set_basis(h64, 0)
+                qv.qv_apply_circuit(h64, (garr, len(gates)), qv.QV_MODE_FUSED, tb)
+            sweep["k=%d" % tb] = _timed(torch, dev, one, 2)
+        res["tile_size_sweep_ms_per_step"] = sweep
+    except Exception as e:  # noqa: BLE001
+        res["tile_size_sweep_ms_per_step"] = {"error": str(e)}
     # 2. complex128 rerun of the bench circuit and its distance to the complex64 result
     try:
         free, _ = torch.cuda.mem_get_info(dev)

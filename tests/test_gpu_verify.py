@@ -97,3 +97,39 @@ def test_distance_mixed_precision(qvlib, orc, cuda):
     assert qv.qv_distance(a, b) == pytest.approx(float(np.linalg.norm(pa - np.eye(1 << n)[1])), rel=1e-9)
     qv.qv_destroy(a)
     qv.qv_destroy(b)
+
+
+def _inverse_random_circuit(gates):
+    """U3(t, p, l)^-1 = U3(-t, -l, -p); CNOT is its own inverse; reversed order."""
+    out = []
+    for g in reversed(gates):
+        if g.kind == "u3":
+            t, p, l = g.theta
+            out.append(g._replace(theta=(-t, -l, -p)))
+        else:
+            out.append(g)
+    return out
+
+
+def test_bench_circuit_30_qubits_properties(qvlib, cuda):
+    """The 30-qubit, 1,780-gate circuit the bench times, at full size, in the
+    bench's launch configuration: the fused passes agree with the per-gate
+    kernels (an independent kernel family), keep the norm, and the inverse
+    circuit brings the state back to |0...0>."""
+    qv = qvlib
+    n, layers = 30, 40
+    gates = W.random_circuit(n, layers, W.config_seed(1))
+    assert len(gates) == 1780
+    hf = qv.qv_create(n, 0)
+    hp = qv.qv_create(n, 0)
+    try:
+        qv.qv_apply_circuit(hf, gates, mode=qv.QV_MODE_FUSED)
+        qv.qv_apply_circuit(hp, gates, mode=qv.QV_MODE_PLAIN)
+        assert qv.qv_distance(hf, hp) <= 1e-5
+        assert abs(qv.qv_norm2(hf) - 1.0) <= 1e-5
+        qv.qv_apply_circuit(hf, _inverse_random_circuit(gates), mode=qv.QV_MODE_FUSED)
+        qv.qv_set_basis(hp, 0)
+        assert qv.qv_distance(hf, hp) <= 2e-5
+    finally:
+        qv.qv_destroy(hf)
+        qv.qv_destroy(hp)

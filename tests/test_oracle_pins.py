@@ -383,3 +383,12 @@ def test_workload_sizes():
     b = W.uneven_batch(64, W.config_seed(4))
     assert len(b) == 64 and all(16 <= n <= 28 and 10 <= d <= 60 for n, d, _ in b)
     assert len(W.ansatz_hamiltonian(20)) == 19 + 20
+
+
+def test_u3_inverse_identity(orc):
+    """U3(t, p, l)^-1 = U3(-t, -l, -p), used to undo the bench circuit on the GPU."""
+    from paper_2508_15545_gb300.workloads import Gate
+    for t, p, l in [(0.3, 1.1, -0.7), (2.9, -2.0, 0.4), (0.0, 0.5, 0.5)]:
+        U = orc.gate_matrix(Gate("u3", 0, theta=(t, p, l)))
+        V = orc.gate_matrix(Gate("u3", 0, theta=(-t, -l, -p)))
+        assert np.allclose(V @ U, np.eye(2), atol=1e-14)
