@@ -1,7 +1,7 @@
 """Builds libqv.so for sm_103a with nvcc: each csrc/*.cu is compiled in
 parallel to an object under _build/, then linked into the package directory.
 
-    python -m paper_2508_15545_gb300.build [--force] [--debug]
+    python -m paper_2508_15545_gb300.build [--force]
 """
 from __future__ import annotations
 
@@ -52,16 +52,16 @@ def _compile(src: str, obj: str, extra) -> str:
     return r.stderr
 
 
-def build(force: bool = False, debug: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
     hdrs = _headers()
-    extra = ["-DQV_DEBUG=1"] if debug else []
+    extra = []
     jobs = []
     objs = []
     for src in srcs:
         stem = os.path.splitext(os.path.basename(src))[0]
-        obj = os.path.join(BUILD, stem + (".dbg.o" if debug else ".o"))
+        obj = os.path.join(BUILD, stem + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + hdrs + [__file__]):
             jobs.append((src, obj))
@@ -85,7 +85,6 @@ def build(force: bool = False, debug: bool = False, verbose: bool = False) -> st
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--force", action="store_true")
-    ap.add_argument("--debug", action="store_true")
     ap.add_argument("-v", "--verbose", action="store_true")
     a = ap.parse_args()
-    print(build(force=a.force, debug=a.debug, verbose=a.verbose))
+    print(build(force=a.force, verbose=a.verbose))
