@@ -304,11 +304,7 @@ qv_status pauli_apply_impl(qv_state *s, const void *src, void *dst, const qv_pau
     if (gbytes > 200 * 1024) return fail(QV_ERR_UNSUPPORTED, "Hamiltonian too large (%zu X-mask groups)", groups.size());
     QV_TRY(ensure_scratch(s, std::max<size_t>(gbytes, 8)));
     if (!groups.empty()) QV_TRY(copy_h2d(s, s->scratch.ptr, groups.data(), gbytes));
-    static bool attr = false;
-    if (!attr) {
-        QV_CUDA(cudaFuncSetAttribute(pauli_apply_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr = true;
-    }
+    QV_TRY(allow_smem(reinterpret_cast<const void *>(pauli_apply_kernel<R>), 200 * 1024));
     prof_bytes(s, QV_K_PAULI, double(dim(s)) * 2 * sizeof(R) * (2 + groups.size()));
     QV_LAUNCH(s, QV_K_PAULI,
               pauli_apply_kernel<R><<<grid_of(s, dim(s)), kThreads, gbytes, s->stream>>>(
@@ -669,7 +665,7 @@ qv_status adjoint_sweep_tiled(qv_state *s, const qv_gate *g, size_t ng, const st
     const int maxg = MaxG<R>::v;
     auto kern = K == 12 ? adj_tile_kernel<R, 12> : K == 11 ? adj_tile_kernel<R, 11> : adj_tile_kernel<R, 10>;
     const size_t smem = smem_bytes<R>(K);
-    QV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    QV_TRY(allow_smem(reinterpret_cast<const void *>(kern), int(smem)));
     int per_sm = 0;
     QV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kT, smem));
     if (per_sm < 1) return fail(QV_ERR_UNSUPPORTED, "tiled reverse sweep does not fit on an SM");

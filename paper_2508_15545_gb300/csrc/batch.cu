@@ -269,12 +269,7 @@ namespace {
 
 template <typename R, int K> qv_status set_attr_once()
 {
-    static bool done = false;
-    if (!done) {
-        QV_CUDA(cudaFuncSetAttribute(batch_kernel<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-        done = true;
-    }
-    return QV_OK;
+    return allow_smem(reinterpret_cast<const void *>(batch_kernel<R, K>), 220 * 1024);
 }
 
 template <typename R, int K> qv_status occupancy(size_t smem, int *per_sm)
@@ -294,8 +289,10 @@ template <typename R> qv_status group_occupancy(int K, size_t smem, int *per_sm)
     }
 }
 
+// Enqueues the group's persistent launch; false when the driver refused the
+// compiled launch (the runtime's error state does not see driver API calls).
 template <typename R>
-void launch_group(qv_batch *b, const BatchGroup &g, unsigned *next)
+bool launch_group(qv_batch *b, const BatchGroup &g, unsigned *next)
 {
     if (g.jit) {
         uint32_t nitems = g.nitems, nchunks = g.nchunks, spin = kSpinLimit;
@@ -303,8 +300,7 @@ void launch_group(qv_batch *b, const BatchGroup &g, unsigned *next)
         void *amps = g.jamps, *coefs = g.jcoefs, *items = g.items, *done = g.done, *st = b->status;
         void *nx = next;
         void *args[] = {&amps, &coefs, &items, &nitems, &nx, &done, &st, &ntiles, &nchunks, &spin};
-        jit_launch_batch(g.jb, b->stream, g.grid, args);  // a failure shows in cudaGetLastError / the capture
-        return;
+        return jit_launch_batch(g.jb, b->stream, g.grid, args) == QV_OK;
     }
     R *const *amps = static_cast<R *const *>(b->amps);
     auto args = [&](auto kern) {
@@ -316,6 +312,7 @@ void launch_group(qv_batch *b, const BatchGroup &g, unsigned *next)
     if (g.K == 10) args(batch_kernel<R, 10>);
     else if (g.K == 11) args(batch_kernel<R, 11>);
     else args(batch_kernel<R, 12>);
+    return true;
 }
 
 qv_status dmalloc(qv_batch *b, void **p, size_t bytes)
@@ -502,7 +499,7 @@ qv_status build(qv_batch *b, const qv_batch_item *items, size_t count, const qv_
         QV_TRY(dmalloc(b, &ee, count * sizeof(double)));
         b->part = static_cast<double *>(pp);
         b->energies = static_cast<double *>(ee);
-        QV_CUDA(cudaFuncSetAttribute(batch_pauli_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        QV_TRY(allow_smem(reinterpret_cast<const void *>(batch_pauli_kernel<R>), 200 * 1024));
     }
     QV_CUDA(cudaMallocHost(reinterpret_cast<void **>(&b->host), (count + 2) * sizeof(double)));
     // ---- capture the whole run in one graph
@@ -523,8 +520,8 @@ qv_status build(qv_batch *b, const qv_batch_item *items, size_t count, const qv_
             ce = cudaGetLastError();
         }
         for (size_t gi = 0; gi < b->groups.size() && ce == cudaSuccess; ++gi) {
-            launch_group<R>(b, b->groups[gi], b->next + gi);
-            ce = cudaGetLastError();
+            const bool ok = launch_group<R>(b, b->groups[gi], b->next + gi);
+            ce = ok ? cudaGetLastError() : cudaErrorLaunchFailure;
         }
         if (nt && ce == cudaSuccess) {
             batch_pauli_kernel<R><<<dim3(kBlocksPerState, unsigned(count)), kBThreads,

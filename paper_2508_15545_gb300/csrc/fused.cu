@@ -93,13 +93,7 @@ template <typename R, int K> size_t smem_for(size_t blob)
 
 template <typename R, int K> qv_status launch_pass(qv_state *s, const unsigned char *dblob, size_t blob)
 {
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(fused_pass_kernel<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        227 * 1024);
-    });
-    QV_CUDA(attr_err);
+    QV_TRY(allow_smem(reinterpret_cast<const void *>(fused_pass_kernel<R, K>), 227 * 1024));
     constexpr int T = 1 << (K - kRegBits);
     const size_t smem = smem_for<R, K>(blob);
     int per_sm = 0;

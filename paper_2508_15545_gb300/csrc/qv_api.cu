@@ -4,6 +4,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+#include <set>
+#include <tuple>
 
 #include "qv_device.cuh"
 #include "qv_internal.h"
@@ -48,6 +51,19 @@ qv_status ensure_scratch(qv_state *s, size_t bytes)
     const size_t b = std::max<size_t>(bytes, 1 << 20);
     QV_CUDA(cudaMalloc(&s->scratch.ptr, b));
     s->scratch.bytes = b;
+    return QV_OK;
+}
+
+qv_status allow_smem(const void *fn, int bytes)
+{
+    static std::mutex mu;
+    static std::set<std::tuple<const void *, int, int>> done;
+    int dev = 0;
+    QV_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({fn, dev, bytes})) return QV_OK;
+    QV_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    done.insert({fn, dev, bytes});
     return QV_OK;
 }
 

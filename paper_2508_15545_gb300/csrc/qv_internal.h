@@ -101,6 +101,9 @@ inline size_t amp_bytes(qv_dtype dt) { return dt == QV_C64 ? 8 : 16; }
 inline uint64_t dim(const qv_state *s) { return uint64_t(1) << s->n; }
 
 qv_status ensure_scratch(qv_state *s, size_t bytes);
+// Raises the dynamic shared-memory limit of kernel `fn` to `bytes` on the
+// current device, once per (kernel, device, bytes); thread-safe.
+qv_status allow_smem(const void *fn, int bytes);
 // Device status word of the handle (allocated and cleared on first use).
 qv_status status_word(qv_state *s, int **out);
 // Synchronises the handle's stream and reports a nonzero status word

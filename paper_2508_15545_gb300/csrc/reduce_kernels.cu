@@ -339,12 +339,7 @@ template <typename R> qv_status pauli_impl(qv_state *s, const qv_pauli_term *ter
         PauliGroupAll *dg = reinterpret_cast<PauliGroupAll *>(base);
         double *part = reinterpret_cast<double *>(base + gb), *res = part + grid;
         QV_TRY(copy_h2d(s, dg, ga.data(), gb));
-        static bool attr[2] = {false, false};
-        if (!attr[sizeof(R) == 8]) {
-            QV_CUDA(cudaFuncSetAttribute(pauli_all_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(kPauliAllSmem)));
-            attr[sizeof(R) == 8] = true;
-        }
+        QV_TRY(allow_smem(reinterpret_cast<const void *>(pauli_all_kernel<R>), int(kPauliAllSmem)));
         prof_bytes(s, QV_K_PAULI, double(dim(s)) * 2 * sizeof(R) * double(ng + 1));
         QV_LAUNCH(s, QV_K_PAULI, pauli_all_kernel<R><<<grid, kThreads, gb, s->stream>>>(
                                       static_cast<const R *>(s->amp), dim(s), dg, int(ng), part));
