@@ -434,6 +434,22 @@ def extras(args, qv, torch, dev, h64, gates):
         res["tile_size_sweep_ms_per_step"] = sweep
     except Exception as e:  # noqa: BLE001
         res["tile_size_sweep_ms_per_step"] = {"error": str(e)}
+    # 1c. the same step with the state in mapped host memory (read and written over NVLink-C2C)
+    try:
+        hh = qv.qv_create(args.n, qv.QV_C64, flags=qv.QV_ALLOC_HOST)
+        garr = qv.gates_to_c(gates)
+
+        def host_step():
+            qv.qv_set_basis(hh, 0)
+            qv.qv_apply_circuit(hh, (garr, len(gates)), qv.QV_MODE_FUSED)
+        ms_h = _timed(torch, dev, host_step, 1)
+        passes = qv.qv_plan_info(args.n, qv.QV_C64, (garr, len(gates)))["passes"]
+        res["host_memory_state"] = {"ms_per_step": ms_h, "updates_per_s": len(gates) * N / (ms_h / 1e3),
+                                    "passes": passes,
+                                    "GBps_over_c2c": 2.0 * passes * N * 8 / (ms_h / 1e3) / 1e9}
+        qv.qv_destroy(hh)
+    except Exception as e:  # noqa: BLE001
+        res["host_memory_state"] = {"error": str(e)}
     # 2. complex128 rerun of the bench circuit and its distance to the complex64 result
     try:
         free, _ = torch.cuda.mem_get_info(dev)

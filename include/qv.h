@@ -115,6 +115,15 @@ typedef struct {
  * device buffer. QV_ERR_OOM if it does not fit. */
 qv_status qv_create(int n, qv_dtype dt, void *cuda_stream, qv_state **out);
 
+/* qv_create with placement flags. QV_ALLOC_HOST puts the amplitudes in
+ * page-locked host memory mapped into the device's address space: the paper
+ * keeps states larger than fast memory in a slower tier (Sec. III-B/C, the
+ * disk and its RAM cache); here that tier is the host memory behind
+ * NVLink-C2C, and every kernel reads and writes it there. QV_ERR_OOM when
+ * the allocation would take more than 3/4 of the host's free memory. */
+#define QV_ALLOC_HOST 1
+qv_status qv_create_ex(int n, qv_dtype dt, void *cuda_stream, int32_t flags, qv_state **out);
+
 /* Wraps a caller-owned device buffer of 2^n amplitudes (interleaved re, im;
  * 16-byte aligned) without copying or initialising it. The buffer must stay
  * valid until qv_destroy; the library never frees it. */

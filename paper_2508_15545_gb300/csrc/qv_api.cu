@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <unistd.h>
 #include <mutex>
 #include <set>
 #include <tuple>
@@ -207,24 +208,50 @@ qv_status qv_wrap(void *dev_ptr, int n, qv_dtype dt, void *cuda_stream, qv_state
 
 qv_status qv_create(int n, qv_dtype dt, void *cuda_stream, qv_state **out)
 {
+    return qv_create_ex(n, dt, cuda_stream, 0, out);
+}
+
+qv_status qv_create_ex(int n, qv_dtype dt, void *cuda_stream, int32_t flags, qv_state **out)
+{
     if (!out) return fail(QV_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (n < 1 || n > 40) return fail(QV_ERR_ARG, "n = %d outside [1, 40]", n);
     if (dt != QV_C64 && dt != QV_C128) return fail(QV_ERR_ARG, "bad dtype %d", int(dt));
+    if (flags & ~int32_t(QV_ALLOC_HOST)) return fail(QV_ERR_ARG, "unknown flags 0x%x", unsigned(flags));
+    const bool host = flags & QV_ALLOC_HOST;
     const size_t bytes = (size_t(1) << n) * amp_bytes(dt);
-    size_t free_b = 0, total_b = 0;
-    cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemGetInfo");
-    if (bytes > free_b) return fail(QV_ERR_OOM, "state needs %zu bytes, %zu free", bytes, free_b);
     void *p = nullptr;
-    e = cudaMalloc(&p, bytes);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(state)");
+    cudaError_t e;
+    if (host) {
+        const long pages = sysconf(_SC_AVPHYS_PAGES), psz = sysconf(_SC_PAGESIZE);
+        const double avail = pages > 0 && psz > 0 ? double(pages) * double(psz) : 0.0;
+        if (double(bytes) > 0.75 * avail)
+            return fail(QV_ERR_OOM, "state needs %zu bytes of host memory, %.0f available", bytes, avail);
+        e = cudaHostAlloc(&p, bytes, cudaHostAllocMapped | cudaHostAllocPortable);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaHostAlloc(state)");
+        void *dp = nullptr;
+        e = cudaHostGetDevicePointer(&dp, p, 0);
+        if (e != cudaSuccess || dp != p) {  // kernels use the host address (unified addressing)
+            cudaFreeHost(p);
+            return e != cudaSuccess ? cuda_fail(e, "cudaHostGetDevicePointer")
+                                    : fail(QV_ERR_UNSUPPORTED, "host memory is not mapped at its own address");
+        }
+    } else {
+        size_t free_b = 0, total_b = 0;
+        e = cudaMemGetInfo(&free_b, &total_b);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemGetInfo");
+        if (bytes > free_b) return fail(QV_ERR_OOM, "state needs %zu bytes, %zu free", bytes, free_b);
+        e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(state)");
+    }
     qv_status st = qv_wrap(p, n, dt, cuda_stream, out);
     if (st != QV_OK) {
-        cudaFree(p);
+        if (host) cudaFreeHost(p);
+        else cudaFree(p);
         return st;
     }
     (*out)->owned = true;
+    (*out)->host_mem = host;
     st = launch_set_basis(*out, 0);
     if (st != QV_OK) {
         qv_destroy(*out);
@@ -242,7 +269,10 @@ qv_status qv_destroy(qv_state *s)
     prof_release(s);
     if (s->scratch.ptr) cudaFree(s->scratch.ptr);
     if (s->host_out) cudaFreeHost(s->host_out);
-    if (s->owned && s->amp) cudaFree(s->amp);
+    if (s->owned && s->amp) {
+        if (s->host_mem) cudaFreeHost(s->amp);
+        else cudaFree(s->amp);
+    }
     if (s->dev_status) cudaFree(s->dev_status);
     delete s;
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
@@ -277,7 +307,7 @@ qv_status qv_get_state(qv_state *s, void *host, size_t bytes)
     CHECK_HANDLE(s);
     if (!host) return fail(QV_ERR_ARG, "host is NULL");
     if (bytes != dim(s) * amp_bytes(s->dt)) return fail(QV_ERR_ARG, "bytes != state size");
-    QV_CUDA(cudaMemcpyAsync(host, s->amp, bytes, cudaMemcpyDeviceToHost, s->stream));
+    QV_CUDA(cudaMemcpyAsync(host, s->amp, bytes, cudaMemcpyDefault, s->stream));
     return sync_and_check(s);
 }
 
@@ -286,7 +316,7 @@ qv_status qv_set_state(qv_state *s, const void *host, size_t bytes)
     CHECK_HANDLE(s);
     if (!host) return fail(QV_ERR_ARG, "host is NULL");
     if (bytes != dim(s) * amp_bytes(s->dt)) return fail(QV_ERR_ARG, "bytes != state size");
-    QV_CUDA(cudaMemcpyAsync(s->amp, host, bytes, cudaMemcpyHostToDevice, s->stream));
+    QV_CUDA(cudaMemcpyAsync(s->amp, host, bytes, cudaMemcpyDefault, s->stream));
     QV_CUDA(cudaStreamSynchronize(s->stream));
     return QV_OK;
 }

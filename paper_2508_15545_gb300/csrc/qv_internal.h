@@ -45,6 +45,7 @@ struct qv_state {
     qv_dtype dt = QV_C64;
     void *amp = nullptr;          // device amplitudes
     bool owned = false;
+    bool host_mem = false;        // amplitudes in mapped page-locked host memory
     cudaStream_t stream = nullptr;
     int device = 0;
     int num_sms = 0;

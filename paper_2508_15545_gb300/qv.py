@@ -21,6 +21,7 @@ QV_MODE_AUTO, QV_MODE_PLAIN, QV_MODE_FUSED = 0, 1, 2
 QV_PLAN_NO_FUSION = 1
 QV_PLAN_INTERPRET = 2
 QV_PLAN_NO_PAIRS = 4
+QV_ALLOC_HOST = 1
 QV_SWEEP_AUTO, QV_SWEEP_PER_GATE, QV_SWEEP_TILES, QV_SWEEP_COMPILED = 0, 1, 2, 3
 STATUS_NAMES = {0: "QV_OK", 1: "QV_ERR_ARG", 2: "QV_ERR_OOM", 3: "QV_ERR_CUDA",
                 4: "QV_ERR_TIMEOUT", 5: "QV_ERR_UNSUPPORTED"}
@@ -76,6 +77,7 @@ def _load():
     P = ctypes.c_void_p
     sig = {
         "qv_create": [ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(_H)],
+        "qv_create_ex": [ctypes.c_int, ctypes.c_int, P, ctypes.c_int32, ctypes.POINTER(_H)],
         "qv_wrap": [P, ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(_H)],
         "qv_destroy": [_H],
         "qv_set_stream": [_H, P],
@@ -191,9 +193,13 @@ def plan_opts(mode: int = QV_MODE_AUTO, tile_bits: int = 0, flags: int = 0) -> q
 # ----------------------------------------------------------------------------
 # C ABI, one Python function per entry point
 # ----------------------------------------------------------------------------
-def qv_create(n: int, dtype: int = QV_C64, stream=None) -> int:
+def qv_create(n: int, dtype: int = QV_C64, stream=None, flags: int = 0) -> int:
+    """New |0...0> state; flags = QV_ALLOC_HOST keeps it in mapped host memory."""
     h = _H()
-    _check(lib.qv_create(n, dtype, _stream_ptr(stream), ctypes.byref(h)))
+    if flags:
+        _check(lib.qv_create_ex(n, dtype, _stream_ptr(stream), flags, ctypes.byref(h)))
+    else:
+        _check(lib.qv_create(n, dtype, _stream_ptr(stream), ctypes.byref(h)))
     return h.value
 
 

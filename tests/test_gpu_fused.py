@@ -179,3 +179,38 @@ def test_plan_cache_follows_the_gate_list(qvlib, orc, cuda):
             assert dist(qv.qv_get_state(h), orc.run(n, gates)) <= TOL[0], (tb, flags)
     finally:
         qv.qv_destroy(h)
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_host_memory_state(qvlib, orc, cuda, dtype):
+    """A state kept in mapped host memory (the slower tier behind NVLink-C2C)
+    goes through the same kernels: fused and per-gate circuits, reductions,
+    the adjoint gradient, and distance to a device-memory copy."""
+    qv = qvlib
+    n = 17
+    gates = W.random_gate_list(n, 150, seed=31, ctrl_prob=0.3)
+    psi = W.random_state(n, 8)
+    want = orc.run(n, gates, psi.copy())
+    hd = qv.qv_create(n, dtype)
+    for mode in (qv.QV_MODE_FUSED, qv.QV_MODE_PLAIN):
+        hh = qv.qv_create(n, dtype, flags=qv.QV_ALLOC_HOST)
+        qv.qv_set_state(hh, psi)
+        qv.qv_apply_circuit(hh, gates, mode=mode)
+        got = qv.qv_get_state(hh)
+        assert dist(got, want) <= TOL[dtype], mode
+        z, _ = qv.qv_expect_z(hh)
+        ref = got.astype(np.complex128)
+        assert np.max(np.abs(np.asarray(z) - orc.expect_z(ref))) <= (1e-6 if dtype == 0 else 1e-12)
+        qv.qv_set_state(hd, psi)
+        qv.qv_apply_circuit(hd, gates, mode=mode)
+        assert qv.qv_distance(hh, hd) <= 2 * TOL[dtype]
+        qv.qv_destroy(hh)
+    # adjoint with psi in host memory (lambda stays on the device)
+    ag, npar = W.ansatz_circuit(12, 2, W.config_seed(3, 9))
+    terms = W.ansatz_hamiltonian(12)
+    hh = qv.qv_create(12, dtype, flags=qv.QV_ALLOC_HOST)
+    g, e = qv.qv_adjoint_grad(hh, ag, terms, npar)
+    ref = orc.param_shift_grad(12, ag, terms, npar)
+    assert np.max(np.abs(g - ref)) <= (1e-4 if dtype == 0 else 1e-10)
+    qv.qv_destroy(hh)
+    qv.qv_destroy(hd)
