@@ -434,6 +434,15 @@ def extras(args, qv, torch, dev, h64, gates):
         res["tile_size_sweep_ms_per_step"] = sweep
     except Exception as e:  # noqa: BLE001
         res["tile_size_sweep_ms_per_step"] = {"error": str(e)}
+    # 1b'. measurement sampling of the bench state: 10^6 shots
+    try:
+        qv.qv_set_basis(h64, 0)
+        qv.qv_apply_circuit(h64, (qv.gates_to_c(gates), len(gates)), qv.QV_MODE_FUSED)
+        u = W.SplitMix64(7).uniform(1000000)
+        ms_s = _timed(torch, dev, lambda: qv.qv_sample(h64, u), 2)
+        res["sampling"] = {"shots": len(u), "ms": ms_s, "shots_per_s": len(u) / (ms_s / 1e3)}
+    except Exception as e:  # noqa: BLE001
+        res["sampling"] = {"error": str(e)}
     # 1c. the same step with the state in mapped host memory (read and written over NVLink-C2C)
     try:
         hh = qv.qv_create(args.n, qv.QV_C64, flags=qv.QV_ALLOC_HOST)

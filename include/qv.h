@@ -257,6 +257,23 @@ qv_status qv_adjoint_grad(qv_state *s, const qv_gate *g, size_t ng, const qv_pau
 qv_status qv_adjoint_grad_ex(qv_state *s, const qv_gate *g, size_t ng, const qv_pauli_term *H, size_t nt,
                              size_t nparams, double *grad_out, double *expval_out, int32_t sweep_mode);
 
+/* ------------------------------------------------------------------------ */
+/* Measurement and partial amplitudes (not in the paper; Sec. III-E notes     */
+/* that its strategies carry over to partial-amplitude simulation)            */
+/* ------------------------------------------------------------------------ */
+
+/* Samples computational-basis outcomes from p_i = |a_i|^2 / sum |a|^2 by
+ * inverse CDF: out[k] = the smallest i with p_0 + ... + p_i > u[k]. The
+ * uniforms u[k] in [0, 1) are inputs (the caller's random numbers); a target
+ * that rounds to the total takes the last outcome of nonzero probability.
+ * Probabilities and sums are FP64. One read of the state plus one read of
+ * each segment of 4096 amplitudes that holds a shot. Synchronises. */
+qv_status qv_sample(qv_state *s, const double *u, size_t nshots, uint64_t *out);
+
+/* Copies amplitudes idx[0..k) to host (interleaved re, im in the state's
+ * precision: 8 or 16 bytes each). Synchronises. */
+qv_status qv_get_amplitudes(qv_state *s, const uint64_t *idx, size_t k, void *host);
+
 /* Distance of the state to the closed form of the quantum Fourier transform
  * of the basis state |j> (the paper's workloads have no QFT; this checks large
  * runs on the GPU): *dist = sqrt( sum_k |a_k - exp(2 pi i (j k mod 2^n) / 2^n)

@@ -206,6 +206,19 @@ def apply_pauli_sum(psi: np.ndarray, terms: Sequence[Tuple[float, int, int]]) ->
     return out
 
 
+def sample(psi: np.ndarray, u) -> np.ndarray:
+    """Born-rule measurement in the computational basis by inverse CDF: for
+    each uniform u in [0, 1), the smallest i with p_0 + ... + p_i > u * sum p,
+    p_i = re_i^2 + im_i^2 (FP64). A target that rounds to the total takes the
+    last outcome with nonzero probability."""
+    p = psi.real.astype(np.float64) ** 2 + psi.imag.astype(np.float64) ** 2
+    cdf = np.cumsum(p)
+    total = cdf[-1]
+    idx = np.searchsorted(cdf, np.asarray(u, dtype=np.float64) * total, side="right")
+    last = int(np.nonzero(p)[0][-1])
+    return np.minimum(idx, last).astype(np.uint64)
+
+
 def inner(a: np.ndarray, b: np.ndarray) -> complex:
     re, im = ctypes.c_double(), ctypes.c_double()
     lib().orc_inner(_ptr(a), _ptr(b), _check_state(a), ctypes.byref(re), ctypes.byref(im))

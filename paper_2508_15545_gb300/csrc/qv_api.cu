@@ -547,6 +547,27 @@ qv_status qv_distance(qv_state *a, qv_state *b, double *out)
     return distance(a, b, out);
 }
 
+qv_status qv_sample(qv_state *s, const double *u, size_t nshots, uint64_t *out)
+{
+    CHECK_HANDLE(s);
+    if (nshots == 0) return QV_OK;
+    if (!u || !out) return fail(QV_ERR_ARG, "u or out is NULL");
+    if (nshots > (size_t(1) << 31)) return fail(QV_ERR_ARG, "at most 2^31 shots per call");
+    for (size_t k = 0; k < nshots; ++k)
+        if (!(u[k] >= 0.0 && u[k] < 1.0)) return fail(QV_ERR_ARG, "u[%zu] = %g outside [0, 1)", k, u[k]);
+    return sample(s, u, nshots, out);
+}
+
+qv_status qv_get_amplitudes(qv_state *s, const uint64_t *idx, size_t k, void *host)
+{
+    CHECK_HANDLE(s);
+    if (k == 0) return QV_OK;
+    if (!idx || !host) return fail(QV_ERR_ARG, "idx or host is NULL");
+    for (size_t j = 0; j < k; ++j)
+        if (idx[j] >= dim(s)) return fail(QV_ERR_ARG, "idx[%zu] = %llu >= 2^n", j, (unsigned long long)idx[j]);
+    return get_amplitudes(s, idx, k, host);
+}
+
 qv_status qv_wait_selftest(qv_state *s, uint32_t limit)
 {
     CHECK_HANDLE(s);

@@ -134,6 +134,10 @@ qv_status validate_gate(const qv_gate &g, int n, size_t idx);
 // ---------------------------------------------------------------- adjoint (adjoint.cu)
 // dst = H src for H = sum of Pauli terms; src, dst: 2^n amplitudes of s's dtype.
 qv_status pauli_apply(qv_state *s, const void *src, void *dst, const qv_pauli_term *terms, size_t nt);
+// Inverse-CDF samples of the Born distribution for uniforms u (sample.cu).
+qv_status sample(qv_state *s, const double *u, size_t nshots, uint64_t *out);
+// Amplitudes idx[0..k) copied to host (interleaved re, im in the state's precision).
+qv_status get_amplitudes(qv_state *s, const uint64_t *idx, size_t k, void *host);
 // sweep: QV_SWEEP_* (qv.h)
 qv_status adjoint_grad(qv_state *s, const qv_gate *g, size_t ng, const qv_pauli_term *H, size_t nt, size_t nparams,
                        double *grad_out, double *expval_out, int sweep);

@@ -110,6 +110,8 @@ def _load():
         "qv_batch_destroy": [ctypes.c_void_p],
         "qv_verify_qft": [_H, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)],
         "qv_sync": [_H],
+        "qv_sample": [_H, P, ctypes.c_size_t, P],
+        "qv_get_amplitudes": [_H, P, ctypes.c_size_t, P],
         "qv_wait_selftest": [_H, ctypes.c_uint32],
         "qv_distance": [_H, _H, ctypes.POINTER(ctypes.c_double)],
         "qv_profile": [_H, ctypes.c_int],
@@ -398,6 +400,23 @@ def qv_verify_qft(h: int, j: int) -> float:
     d = ctypes.c_double()
     _check(lib.qv_verify_qft(h, j, ctypes.byref(d)))
     return d.value
+
+
+def qv_sample(h: int, u) -> np.ndarray:
+    """Outcomes for the uniforms u in [0, 1) (inverse-CDF sampling of |a|^2)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.zeros(max(1, u.size), dtype=np.uint64)
+    _check(lib.qv_sample(h, u.ctypes.data, u.size, out.ctypes.data))
+    return out[:u.size]
+
+
+def qv_get_amplitudes(h: int, idx) -> np.ndarray:
+    """Amplitudes at the given indices (complex64 or complex128 as the state)."""
+    _, dt, _ = qv_info(h)
+    idx = np.ascontiguousarray(idx, dtype=np.uint64)
+    out = np.zeros(max(1, idx.size), dtype=np.complex64 if dt == QV_C64 else np.complex128)
+    _check(lib.qv_get_amplitudes(h, idx.ctypes.data, idx.size, out.ctypes.data))
+    return out[:idx.size]
 
 
 def qv_sync(h: int):

@@ -210,3 +210,48 @@ def test_expect_pauli_one_pass_and_many_groups(qvlib, orc, cuda, dtype, nterms):
     want = orc.expect_terms(ref, terms)
     assert abs(got - want) <= (2e-5 if dtype == 0 else 1e-11) * sum(abs(t[0]) for t in terms)
     qv.qv_destroy(h)
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("n", [3, 13, 18])
+def test_sample_matches_oracle(qvlib, orc, cuda, dtype, n):
+    """Inverse-CDF samples equal the oracle's on the same uniforms and the same
+    stored amplitudes (bit-exact indices; a target within rounding of a
+    cumulative boundary may take either neighbour, checked for validity)."""
+    qv = qvlib
+    psi = W.random_state(n, 500 + n)
+    if n == 13:
+        psi[: 1 << 10] = 0          # a run of zero-probability outcomes
+        psi /= np.linalg.norm(psi)
+    h = qv.qv_create(n, dtype)
+    qv.qv_set_state(h, psi)
+    stored = qv.qv_get_state(h).astype(np.complex128)
+    u = np.concatenate([W.SplitMix64(n).uniform(3000), [0.0, np.nextafter(1.0, 0.0)]])
+    got = qv.qv_sample(h, u)
+    want = orc.sample(stored, u)
+    p = stored.real ** 2 + stored.imag ** 2
+    cdf = np.cumsum(p)
+    for k in np.nonzero(got != want)[0]:
+        i, t = int(got[k]), u[k] * cdf[-1]
+        assert p[i] > 0 and cdf[i] >= t - 1e-12 * cdf[-1] and (i == 0 or cdf[i - 1] <= t + 1e-12 * cdf[-1])
+    assert np.count_nonzero(got != want) <= 1
+    idx = np.array([0, (1 << n) - 1, 5 % (1 << n), 7 % (1 << n)], dtype=np.uint64)
+    amps = qv.qv_get_amplitudes(h, idx)
+    assert np.array_equal(amps, qv.qv_get_state(h)[idx.astype(np.int64)])
+    with pytest.raises(qv.QvError):
+        qv.qv_sample(h, [1.0])
+    with pytest.raises(qv.QvError):
+        qv.qv_get_amplitudes(h, [1 << n])
+    qv.qv_destroy(h)
+
+
+def test_sample_basis_and_ghz(qvlib, cuda):
+    qv = qvlib
+    h = qv.qv_create(20, 0)
+    qv.qv_set_basis(h, 123457)
+    assert np.all(qv.qv_sample(h, np.linspace(0, 0.999, 50)) == 123457)
+    qv.qv_set_basis(h, 0)
+    qv.qv_apply_circuit(h, W.ghz_circuit(20))
+    s = qv.qv_sample(h, np.linspace(0, 0.999, 200))
+    assert set(int(x) for x in s) == {0, (1 << 20) - 1}
+    qv.qv_destroy(h)

@@ -392,3 +392,28 @@ def test_u3_inverse_identity(orc):
         U = orc.gate_matrix(Gate("u3", 0, theta=(t, p, l)))
         V = orc.gate_matrix(Gate("u3", 0, theta=(-t, -l, -p)))
         assert np.allclose(V @ U, np.eye(2), atol=1e-14)
+
+
+def test_sample_pins(orc):
+    """Inverse-CDF sampling: a basis state always gives its index; a known
+    distribution gives the outcomes its cumulative sums fix, skipping
+    zero-probability outcomes; brute force on a random small state."""
+    psi = orc.basis(5, 19)
+    assert np.all(orc.sample(psi, [0.0, 0.3, 0.999999]) == 19)
+    amp = np.array([0.5, 0, 0.5j, 0, -0.5, 0.5, 0, 0], dtype=np.complex128)   # p = 1/4 at 0, 2, 4, 5 (exact)
+    got = orc.sample(amp, [0.0, 0.1, 0.25, 0.5, 0.7499, 0.75, 0.99, np.nextafter(1.0, 0.0)])
+    assert [int(x) for x in got] == [0, 0, 2, 4, 4, 5, 5, 5]
+    amp0 = np.array([0.6, 0.8, 0.0, 0.0], dtype=np.complex128)   # last outcomes have p = 0
+    assert orc.sample(amp0, [np.nextafter(1.0, 0.0)])[0] == 1
+    rng = np.random.default_rng(3)
+    psi = W.random_state(6, 44)
+    u = rng.random(300)
+    p = np.abs(psi) ** 2
+    for uk, ik in zip(u, orc.sample(psi, u)):
+        acc, want = 0.0, None
+        for i, pi in enumerate(p):          # first index whose running sum exceeds u * total
+            acc += pi
+            if acc > uk * p.sum():
+                want = i
+                break
+        assert int(ik) == want
