@@ -133,3 +133,69 @@ def test_bench_circuit_30_qubits_properties(qvlib, cuda):
     finally:
         qv.qv_destroy(hf)
         qv.qv_destroy(hp)
+
+
+def test_batch_256_ansatz_20_qubits_full_size(qvlib, orc, cuda):
+    """The batched workload at full size (256 parameter sets of the 20-qubit,
+    12-layer ansatz, <H> each, one graph), as the bench runs it: four sampled
+    members against the oracle's energy, every member within the spectral
+    bound ||H||_1 and against the one-by-one GPU path."""
+    qv = qvlib
+    n, layers, count = 20, 12, 256
+    terms = W.ansatz_hamiltonian(n)
+    circuits = [W.ansatz_circuit(n, layers, W.config_seed(2, c))[0] for c in range(count)]
+    states = [qv.qv_create(n, 0) for _ in range(count)]
+    try:
+        b = qv.Batch(list(zip(states, circuits)), terms)
+        e = b.run()
+        l1 = sum(abs(c) for c, _, _ in terms)
+        assert np.all(np.abs(e) <= l1 + 1e-9)
+        for c in (0, 77, 128, 255):
+            assert e[c] == pytest.approx(orc.energy(n, circuits[c], terms), abs=1e-4), c
+        h = qv.qv_create(n, 0)
+        for c in range(0, count, 37):
+            qv.qv_set_basis(h, 0)
+            qv.qv_apply_circuit(h, circuits[c])
+            assert e[c] == pytest.approx(qv.qv_expect_pauli(h, terms), abs=1e-5), c
+        qv.qv_destroy(h)
+        b.close()
+    finally:
+        for h in states:
+            qv.qv_destroy(h)
+
+
+def test_adjoint_26_qubits_full_size(qvlib, cuda):
+    """The gradient workload at full size (26-qubit ansatz, 16 layers, 832
+    parameters): the compiled sweep against the per-gate sweep (an independent
+    kernel family) on every parameter, and three sampled parameters against
+    central differences of GPU energies (h = 1e-3, O(h^2))."""
+    qv = qvlib
+    n, layers = 26, 16
+    gates, npar = W.ansatz_circuit(n, layers, W.config_seed(3))
+    terms = W.ansatz_hamiltonian(n)
+    h = qv.qv_create(n, 0)
+    try:
+        g3, e3 = qv.qv_adjoint_grad(h, gates, terms, npar, sweep_mode=qv.QV_SWEEP_COMPILED)
+        qv.qv_set_basis(h, 0)
+        g1, e1 = qv.qv_adjoint_grad(h, gates, terms, npar, sweep_mode=qv.QV_SWEEP_PER_GATE)
+        assert np.max(np.abs(g3 - g1)) <= 1e-5
+        assert e3 == pytest.approx(e1, abs=1e-6)
+        params = np.zeros(npar)
+        for g in gates:
+            for a, p in enumerate(g.param):
+                if p >= 0:
+                    params[p] = g.theta[a]
+
+        def energy(pv):
+            qv.qv_set_basis(h, 0)
+            qv.qv_apply_circuit(h, W.with_params(gates, pv))
+            return qv.qv_expect_pauli(h, terms)
+        hstep = 1e-3
+        for p in (0, 417, npar - 1):
+            up, dn = params.copy(), params.copy()
+            up[p] += hstep
+            dn[p] -= hstep
+            fd = (energy(up) - energy(dn)) / (2 * hstep)
+            assert g3[p] == pytest.approx(fd, abs=1e-2), p  # FP32 energies, divided by 2h
+    finally:
+        qv.qv_destroy(h)
