@@ -434,6 +434,17 @@ def extras(args, qv, torch, dev, h64, gates):
         res["tile_size_sweep_ms_per_step"] = sweep
     except Exception as e:  # noqa: BLE001
         res["tile_size_sweep_ms_per_step"] = {"error": str(e)}
+    # 1a. qubit remap (Sec. III-E): reverse all qubit positions; SWAPs are relabels inside tiles,
+    # so the passes only move data (HBM-bound)
+    try:
+        perm = list(range(args.n - 1, -1, -1))
+        swaps = [W.Gate("swap", p, target2=args.n - 1 - p) for p in range(args.n // 2)]
+        rp = qv.qv_plan_info(args.n, qv.QV_C64, swaps)["passes"]
+        ms_r = _timed(torch, dev, lambda: qv.qv_permute_qubits(h64, perm), 3)
+        gbs = 2.0 * rp * N * 8 / (ms_r / 1e3) / 1e9
+        res["qubit_reversal"] = {"passes": rp, "ms": ms_r, "GBps": gbs, "frac_of_measured_hbm": gbs / peak}
+    except Exception as e:  # noqa: BLE001
+        res["qubit_reversal"] = {"error": str(e)}
     # 1b'. measurement sampling of the bench state: 10^6 shots
     try:
         qv.qv_set_basis(h64, 0)

@@ -12,7 +12,6 @@
 //     shared memory and a binary search per shot.
 #include <algorithm>
 #include <cmath>
-#include <numeric>
 #include <vector>
 
 #include "qv_device.cuh"
@@ -137,9 +136,11 @@ template <typename R> qv_status sample_impl(qv_state *s, const double *u, size_t
         if (!(t < total) || i > last) i = last;
         sseg[k] = i;
     }
-    std::vector<uint32_t> order(nshots);
-    std::iota(order.begin(), order.end(), 0u);
-    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return sseg[x] < sseg[y]; });
+    // shots in segment order (counting sort over the segments)
+    std::vector<uint32_t> count(nseg + 1, 0), order(nshots);
+    for (size_t k = 0; k < nshots; ++k) ++count[sseg[k] + 1];
+    for (uint64_t i = 0; i < nseg; ++i) count[i + 1] += count[i];
+    for (size_t k = 0; k < nshots; ++k) order[count[sseg[k]]++] = uint32_t(k);
     std::vector<uint64_t> segs;
     std::vector<uint32_t> first;
     std::vector<double> local(nshots);
