@@ -264,7 +264,7 @@ def run_ours(args):
     plan_cost = None
     if mode == qv.QV_MODE_FUSED:
         cfg["plan"] = qv.qv_plan_info(args.n, qv.QV_C64, (garr, ng), args.tile_bits)
-        cfg["tile_bits"] = args.tile_bits or min(args.n, 12)
+        cfg["tile_bits"] = args.tile_bits or qv.qv_default_tile_bits(args.n, qv.QV_C64)
         plan_cost = qv.qv_plan_cost(args.n, qv.QV_C64, (garr, ng), args.tile_bits)
     N = 1 << args.n
 

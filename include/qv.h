@@ -187,6 +187,12 @@ qv_status qv_plan_info(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv
  * operations / arithmetic peak. */
 qv_status qv_plan_cost(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, double out[2]);
 
+/* The tile size (log2 amplitudes) fused mode uses for an n-qubit state of
+ * dtype dt when qv_plan_opts.tile_bits is 0: the autotuner's choice for
+ * (n, dt, engine) if it ran in this process, else a measured default
+ * (2^11 for the compiled complex64 pass, 2^12 otherwise), at most n. Host only. */
+int32_t qv_default_tile_bits(int n, qv_dtype dt, int32_t flags);
+
 /* Autotuner: runs g[0..ng) in fused mode with every supported tile size
  * (2^10 .. 2^12 amplitudes, at most 2^n), times each with CUDA events after a
  * warm-up run, and remembers the fastest for this (n, dtype, engine) -- later

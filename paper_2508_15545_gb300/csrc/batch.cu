@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(1 << (K - kRegBits), 1)
                 if (s > 0) transpose<K, NQ>(tile, stg[s - 1], stg[s], tid, x);
                 run_ops<R>(ops + stg[s].op_begin, stg[s].op_end - stg[s].op_begin, tid, base, x);
             }
+            if (h.nstages == 1) __syncthreads();  // loads of other warps before a relabelled store
             store_tile<NQ>(amp, base, stg[h.nstages - 1].Po, stg[h.nstages - 1].Qo, tid, phys_hi, x);
         }
         __syncthreads();

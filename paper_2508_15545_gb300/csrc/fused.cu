@@ -82,6 +82,9 @@ __global__ void __launch_bounds__(1 << (K - kRegBits), QV_FUSED_MINB(R, K)) fuse
             if (s > 0) transpose<K, NQ>(tile, stg[s - 1], stg[s], tid, x);
             run_ops<R>(ops + stg[s].op_begin, stg[s].op_end - stg[s].op_begin, tid, base, x);
         }
+        // With one stage no transpose separates the loads from the stores; a SWAP
+        // relabel can send a warp's data to positions another warp still has to load.
+        if (nstages == 1) __syncthreads();
         store_tile<NQ>(amp, base, stg[nstages - 1].Po, stg[nstages - 1].Qo, tid, phys_hi, x);
     }
 }
@@ -179,7 +182,8 @@ qv_status to_pgates(const qv_gate *g, size_t ng, std::vector<plan::PGate> &out)
 qv_status plan_info(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t out[4],
                     double cost[2])
 {
-    int K = (opts && opts->tile_bits) ? opts->tile_bits : std::min(n, plan::kMaxK);
+    int K = (opts && opts->tile_bits) ? opts->tile_bits
+                                      : tuned_tile_bits(n, dt, opts && (opts->flags & QV_PLAN_INTERPRET));
     if (K < plan::kMinK || K > plan::kMaxK || K > n) return fail(QV_ERR_ARG, "tile_bits %d unsupported for n = %d", K, n);
     std::vector<plan::PGate> pg;
     QV_TRY(to_pgates(g, ng, pg));

@@ -13,6 +13,7 @@
 #include <nvrtc.h>
 
 #include <algorithm>
+#include <cstring>
 #include <cstdio>
 #include <map>
 #include <memory>
@@ -459,10 +460,15 @@ void emit_op_c128(std::ostream &o, const plan::Op &op, int k)
     }
 }
 
-// CTAs per SM the compiled pass is built for (its register budget). Measured on
-// the 30-qubit random circuit: complex64 K = 11 runs 5 % faster at 6 than at 4,
-// K = 10 5 % faster at 12 than at 8; K = 12 is fastest at 3.
-int min_blocks(bool c64, int k) { return k == 12 ? (c64 ? 3 : 1) : k == 11 ? (c64 ? 6 : 2) : (c64 ? 12 : 2); }
+// CTAs per SM the compiled pass is built for (its register budget). The
+// complex64 pass holds the next tile's loads in registers while it computes
+// the current one, which needs 128 registers: measured on the 30-qubit random
+// circuit, K = 12 at 2 CTAs per SM runs 292 ms (3: 326 ms, spilling), K = 11
+// at 4 runs 285 ms (5: 305, 6: 322), K = 10 at 8 runs 288 ms (12: 317).
+int min_blocks(bool c64, int k) { return k == 12 ? (c64 ? 2 : 1) : k == 11 ? (c64 ? 4 : 2) : (c64 ? 8 : 2); }
+// The same for complex64 tile code without the register-held next tile (the
+// batch kernel): 80 registers, 3 / 6 / 12 CTAs per SM.
+int min_blocks_unpipelined(int k) { return k == 12 ? 3 : k == 11 ? 6 : 12; }
 
 // Thread-invariant offsets of a pass: global offsets of the load and store
 // layouts and the shared-memory word offsets of every transpose.
@@ -492,7 +498,17 @@ void emit_pass_consts(std::ostream &o, const plan::Pass &p, bool c64)
 // transposes and ops, store. Coefficients are read as cf.c[...]; with
 // l2_loads the tile is read through L2 only (other CTAs may have written it
 // since this SM last cached it).
-void emit_tile_body(std::ostream &o, const plan::Pass &p, bool c64, bool l2_loads)
+// Tile base index of tile expression `t` (the bits outside the tile).
+std::string tile_base_expr(const plan::Pass &p, const std::string &t)
+{
+    std::string e = "0ull";
+    for (int s = 0; s < p.nseg; ++s)
+        e += " | (((" + t + " >> " + std::to_string(p.seg_src[s]) + ") & " +
+             hex64((uint64_t(1) << p.seg_w[s]) - 1) + ") << " + std::to_string(p.seg_dst[s]) + ")";
+    return e;
+}
+
+void emit_tile_body(std::ostream &o, const plan::Pass &p, bool c64, bool l2_loads, bool pipelined = false)
 {
     PassGeom G{p.k, p.k - kRegBits, p.k - kChunkBits, &p};
     const int nops = int(p.ops.size());
@@ -513,7 +529,19 @@ void emit_tile_body(std::ostream &o, const plan::Pass &p, bool c64, bool l2_load
             if ((v >> j) & 1) l |= 1u << P[j];
         return l;
     };
-    if (c64) {
+    if (c64 && pipelined) {
+        // this tile was loaded during the previous one; start loading the next
+        o << "    u64 r[8], i[8];\n";
+        for (int v = 0; v < 8; ++v)
+            o << "    r[" << v << "] = pk(nf" << v << ".x, nf" << v << ".z); i[" << v << "] = pk(nf" << v << ".y, nf" << v
+              << ".w);\n";
+        o << "    { const u64 tn = t + gridDim.x;\n";
+        o << "      if (tn < ntiles) { const float *a = amp + 2 * ((" << tile_base_expr(p, "tn") << ") + gL);\n";
+        for (int v = 0; v < 8; ++v)
+            o << "        nf" << v << " = *reinterpret_cast<const float4 *>(a + 2 * " << hex64(G.phys(reg_offset(s0.in.P, v)))
+              << ");\n";
+        o << "      }\n    }\n";
+    } else if (c64) {
         o << "    u64 r[8], i[8];\n";
         o << "    { const float *a = amp + 2 * (base + gL);\n";
         for (int v = 0; v < 8; ++v)
@@ -570,6 +598,10 @@ void emit_tile_body(std::ostream &o, const plan::Pass &p, bool c64, bool l2_load
             else emit_op_c128(o, p.ops[k], k);
         }
     }
+    // With one stage no transpose (and its barrier) separates the loads from the
+    // stores; when SWAP relabels changed the layout, a warp may store into
+    // positions another warp has not loaded yet.
+    if (p.stages.size() == 1 && std::memcmp(&s0.in, &sl.out, sizeof(plan::Layout)) != 0) o << "    __syncthreads();\n";
     if (c64) {
         o << "    { float *a = amp + 2 * (base + gS); float x0, x1, y0, y1;\n";
         for (int v = 0; v < 8; ++v)
@@ -601,8 +633,23 @@ std::string gen_source(const plan::Pass &p, bool c64)
     o << "    extern __shared__ __align__(16) u64 sm[];\n";
     o << "    const u32 tid = threadIdx.x;\n";
     emit_pass_consts(o, p, c64);
+    const bool pipe = c64;
+    if (pipe) {  // prologue: the first tile's loads
+        const plan::Stage &s0 = p.stages.front();
+        PassGeom G{p.k, p.k - kRegBits, p.k - kChunkBits, &p};
+        o << "    float4 nf0, nf1, nf2, nf3, nf4, nf5, nf6, nf7;\n";
+        o << "    if (blockIdx.x < ntiles) { const float *a = amp + 2 * ((" << tile_base_expr(p, "(u64)blockIdx.x")
+          << ") + gL);\n";
+        for (int v = 0; v < 8; ++v) {
+            uint32_t l = 0;
+            for (int j = 0; j < 3; ++j)
+                if ((v >> j) & 1) l |= 1u << s0.in.P[j];
+            o << "      nf" << v << " = *reinterpret_cast<const float4 *>(a + 2 * " << hex64(G.phys(l)) << ");\n";
+        }
+        o << "    }\n";
+    }
     o << "    for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {\n";
-    emit_tile_body(o, p, c64, false);
+    emit_tile_body(o, p, c64, false, pipe);
     o << "    }\n}\n";
     return o.str();
 }
@@ -641,7 +688,7 @@ std::string gen_source_batch(const std::vector<plan::Pass> &passes, int stride, 
     std::ostringstream o;
     o << kPrelude;
     o << "QI u32 ld_acq(const unsigned *p) { u32 v; asm volatile(\"ld.acquire.gpu.global.u32 %0, [%1];\" : \"=r\"(v) : \"l\"(p) : \"memory\"); return v; }\n";
-    o << "extern \"C\" __global__ void __launch_bounds__(" << T << ", " << min_blocks(true, k)
+    o << "extern \"C\" __global__ void __launch_bounds__(" << T << ", " << min_blocks_unpipelined(k)
       << ") qv_batch(float *const *amps, const u64 *__restrict__ coefs, const uint2 *__restrict__ items, u32 nitems, "
          "unsigned *next, unsigned *done, int *status, u64 ntiles, u32 nchunks, u32 spin_limit)\n{\n";
     o << "    extern __shared__ __align__(16) u64 sm[];\n";
@@ -879,6 +926,7 @@ std::string gen_source_adj(const plan::Pass &p, int nslots)
         }
         for (int k = st.op_begin; k < st.op_end; ++k) emit_adj_op_c64(o, p.ops[k], coff[k], lsl[k]);
     }
+    if (p.stages.size() == 1 && std::memcmp(&s0.in, &sl.out, sizeof(plan::Layout)) != 0) o << "    __syncthreads();\n";
     for (int b = 0; b < 2; ++b) {
         const char *dst = b ? "lam" : "amp";
         const char *R = b ? "rl" : "r", *I = b ? "il" : "i";

@@ -547,6 +547,12 @@ qv_status qv_distance(qv_state *a, qv_state *b, double *out)
     return distance(a, b, out);
 }
 
+int32_t qv_default_tile_bits(int n, qv_dtype dt, int32_t flags)
+{
+    if (n < 1 || n > 40) return 0;
+    return tuned_tile_bits(n, dt, (flags & QV_PLAN_INTERPRET) != 0);
+}
+
 qv_status qv_sample(qv_state *s, const double *u, size_t nshots, uint64_t *out)
 {
     CHECK_HANDLE(s);

@@ -110,6 +110,7 @@ def _load():
         "qv_batch_destroy": [ctypes.c_void_p],
         "qv_verify_qft": [_H, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)],
         "qv_sync": [_H],
+        "qv_default_tile_bits": [ctypes.c_int, ctypes.c_int, ctypes.c_int32],
         "qv_sample": [_H, P, ctypes.c_size_t, P],
         "qv_get_amplitudes": [_H, P, ctypes.c_size_t, P],
         "qv_wait_selftest": [_H, ctypes.c_uint32],
@@ -259,6 +260,11 @@ def qv_apply_circuit(h: int, gates, mode: int = QV_MODE_AUTO, tile_bits: int = 0
         arr, ng = gates_to_c(gates), len(gates)
     opts = plan_opts(mode, tile_bits, flags)
     _check(lib.qv_apply_circuit(h, arr, ng, ctypes.byref(opts)))
+
+
+def qv_default_tile_bits(n: int, dtype: int = QV_C64, flags: int = 0) -> int:
+    """Tile size (log2 amplitudes) fused mode uses when none is given."""
+    return int(lib.qv_default_tile_bits(n, dtype, flags))
 
 
 def qv_plan_info(n: int, dtype: int, gates, tile_bits: int = 0, flags: int = 0) -> dict:

@@ -214,3 +214,42 @@ def test_host_memory_state(qvlib, orc, cuda, dtype):
     assert np.max(np.abs(g - ref)) <= (1e-4 if dtype == 0 else 1e-10)
     qv.qv_destroy(hh)
     qv.qv_destroy(hd)
+
+
+@pytest.mark.parametrize("n", [24, 28])
+@pytest.mark.parametrize("k", [10, 11, 12])
+def test_qft_with_swaps_large(qvlib, cuda, n, k):
+    """QFT with its final qubit-reversal SWAPs on states of many tiles. The
+    SWAPs become relabels that can leave a pass with a single stage; its
+    warps must not store into positions other warps still have to load
+    (this caught such a race)."""
+    qv = qvlib
+    j = int(W.SplitMix64(W.config_seed(4, 98)).integers(0, (1 << n) - 1, 1)[0])
+    h = qv.qv_create(n, 0)
+    try:
+        qv.qv_set_basis(h, j)
+        qv.qv_apply_circuit(h, W.qft_circuit(n), mode=qv.QV_MODE_FUSED, tile_bits=k)
+        assert qv.qv_verify_qft(h, j) <= 1e-5
+    finally:
+        qv.qv_destroy(h)
+
+
+@pytest.mark.parametrize("k", [10, 12])
+def test_permutation_passes_24q(qvlib, orc, cuda, k):
+    """Pure relabel passes (random qubit permutations) on a 24-qubit state,
+    against the oracle's index permutation."""
+    qv = qvlib
+    n = 24
+    psi = W.random_state(n, 91)
+    rng = W.SplitMix64(17)
+    h = qv.qv_create(n, 0)
+    try:
+        qv.qv_set_state(h, psi)
+        want = psi.astype(np.complex64).astype(np.complex128)
+        for rep in range(3):
+            perm = [int(x) for x in np.argsort(rng.uniform(n))]
+            qv.qv_permute_qubits(h, perm)
+            want = orc.permute(want, perm)
+        assert dist(qv.qv_get_state(h), want) <= 1e-6
+    finally:
+        qv.qv_destroy(h)
