@@ -190,7 +190,9 @@ qv_status qv_plan_cost(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv
 /* The tile size (log2 amplitudes) fused mode uses for an n-qubit state of
  * dtype dt when qv_plan_opts.tile_bits is 0: the autotuner's choice for
  * (n, dt, engine) if it ran in this process, else a measured default
- * (2^11 for the compiled complex64 pass, 2^12 otherwise), at most n. Host only. */
+ * (2^11 for the compiled complex64 pass, 2^12 otherwise), at most n. A state
+ * created with QV_ALLOC_HOST always takes 2^12 (at most n): its passes are bound
+ * by the host link, so the fewest passes win. Host only. */
 int32_t qv_default_tile_bits(int n, qv_dtype dt, int32_t flags);
 
 /* Autotuner: runs g[0..ng) in fused mode with every supported tile size
