@@ -386,7 +386,6 @@ bool make_plan(int n, int k, bool pin0, bool fuse, bool pairs, const std::vector
     while (!rem.empty()) {
         // ---- choose the tile's high qubits greedily
         std::vector<char> inS(n, 0);
-        for (int q = 0; q < kChunkBits; ++q) inS[q] = 1;
         auto fits = [&](const PGate &g) {
             int need[2];
             const int nn = needs(g, need);
@@ -394,31 +393,49 @@ bool make_plan(int n, int k, bool pin0, bool fuse, bool pairs, const std::vector
                 if (!inS[need[i]]) return false;
             return true;
         };
-        for (int step = 0; step < nh; ++step) {
-            int best = -1;
-            long long best_score = -1;
-            for (int q = kChunkBits; q < n; ++q) {
-                if (inS[q]) continue;
-                inS[q] = 1;
-                const int cnt = scan(gates, rem, n, fits, nullptr);
-                inS[q] = 0;
-                int soon = 0;  // tie-break: gates needing q soon
-                for (size_t r = 0; r < rem.size() && r < size_t(kLookahead); ++r) {
-                    int need[2];
-                    const int nn = needs(gates[rem[r]], need);
-                    for (int i = 0; i < nn; ++i) soon += need[i] == q;
-                }
-                const long long score = (long long)cnt * 4096 + soon * 16 + (n - q);
-                if (score > best_score) {
-                    best_score = score;
-                    best = q;
-                }
+        // Adding one qubit at a time can miss a gate that needs two (a SWAP of two
+        // qubits outside the tile that everything else waits behind); then the
+        // first gate's qubits are put in first, which always makes progress.
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            std::fill(inS.begin(), inS.end(), 0);
+            for (int q = 0; q < kChunkBits; ++q) inS[q] = 1;
+            int steps = nh;
+            if (attempt == 1) {
+                int need[2];
+                const int nn = needs(gates[rem[0]], need);
+                for (int i = 0; i < nn; ++i)
+                    if (!inS[need[i]]) {
+                        inS[need[i]] = 1;
+                        --steps;
+                    }
             }
-            if (best < 0) {
-                err = "no qubit left to add to the tile";
-                return false;
+            for (int step = 0; step < steps; ++step) {
+                int best = -1;
+                long long best_score = -1;
+                for (int q = kChunkBits; q < n; ++q) {
+                    if (inS[q]) continue;
+                    inS[q] = 1;
+                    const int cnt = scan(gates, rem, n, fits, nullptr);
+                    inS[q] = 0;
+                    int soon = 0;  // tie-break: gates needing q soon
+                    for (size_t r = 0; r < rem.size() && r < size_t(kLookahead); ++r) {
+                        int need[2];
+                        const int nn = needs(gates[rem[r]], need);
+                        for (int i = 0; i < nn; ++i) soon += need[i] == q;
+                    }
+                    const long long score = (long long)cnt * 4096 + soon * 16 + (n - q);
+                    if (score > best_score) {
+                        best_score = score;
+                        best = q;
+                    }
+                }
+                if (best < 0) {
+                    err = "no qubit left to add to the tile";
+                    return false;
+                }
+                inS[best] = 1;
             }
-            inS[best] = 1;
+            if (scan(gates, rem, n, fits, nullptr) > 0) break;
         }
         Pass P;
         P.k = k;

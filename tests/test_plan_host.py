@@ -76,3 +76,18 @@ def test_plan_cost_rejects_bad_args(qv):
         qv.qv_plan_cost(0, 0, [Gate("h", 0)])
     with pytest.raises(qv.QvError):
         qv.qv_plan_cost(12, 0, [Gate("h", 12)], tile_bits=10)
+
+
+@pytest.mark.parametrize("flags", [0, 1, 2])
+def test_swap_of_two_outside_qubits_first(qv, flags):
+    """A SWAP of two qubits outside the low chunk heads the gate list and every
+    other gate waits behind it (controlled by one of its qubits), while other
+    qubits are wanted as targets more often: the tile must still take both
+    qubits of the SWAP, or the planner makes no progress."""
+    n = 15
+    gates = [Gate("swap", 10, target2=8)]
+    for q in (5, 6, 7, 9, 11, 12, 13, 14):
+        gates += [Gate("x", q, ctrl=10)] * 10
+    info = qv.qv_plan_info(n, 0, gates, tile_bits=10, flags=flags)
+    assert info["passes"] >= 1
+
