@@ -4,11 +4,16 @@
 // Sampling is inverse-CDF sampling of the Born distribution p_i = |a_i|^2 /
 // sum |a|^2: for a uniform u in [0, 1), the outcome is the smallest i whose
 // cumulative probability exceeds u. The uniforms are inputs. Probabilities and
-// all sums are FP64 (a squared FP32 component is exact in FP64).
+// all sums are FP64 (a squared FP32 component is exact in FP64). Every step
+// runs on the device:
 //  1. per segment of kSeg amplitudes: its probability sum (one read of the state);
-//  2. host: compensated prefix over the segments, then each shot's segment by
-//     binary search and its offset inside the segment;
-//  3. per segment holding shots: an inclusive FP64 scan of its probabilities in
+//  2. one block: compensated exclusive prefix P over the segments (P[nseg] = total)
+//     and the last segment of nonzero probability;
+//  3. per shot: its segment by binary search over P (upper bound of u * total),
+//     counted per segment;
+//  4. one block: exclusive prefix of the counts; then each shot's place in the
+//     shot list ordered by segment (counting sort);
+//  5. per segment holding shots: an inclusive FP64 scan of its probabilities in
 //     shared memory and a binary search per shot.
 #include <algorithm>
 #include <cmath>
@@ -23,6 +28,7 @@ namespace {
 constexpr int kSegBitsS = 12;  // amplitudes per segment: 4096
 constexpr int kSeg = 1 << kSegBitsS;
 constexpr int kThreadsS = 256;
+constexpr int kScanThreads = 1024;  // one block for the prefix over segments
 
 template <typename R> __device__ __forceinline__ double prob(const R *a, uint64_t i)
 {
@@ -53,34 +59,144 @@ __global__ void __launch_bounds__(kThreadsS) seg_prob_kernel(const R *__restrict
     }
 }
 
-// One block per segment that holds shots: segments[b], shots [first[b], first[b+1]).
-// local[k] = the shot's target measured from the segment's start.
-template <typename R>
-__global__ void __launch_bounds__(kThreadsS) seg_search_kernel(const R *__restrict__ a, uint64_t N,
-                                                               const uint64_t *segments, const uint32_t *first,
-                                                               const double *local, uint64_t *out)
+// Exclusive compensated prefix over x[0..m): P[i] = x[0] + ... + x[i-1],
+// P[m] = the total; *last = the largest i with x[i] > 0 (left as set when none).
+// One block: each thread sums a contiguous run, thread 0 chains the runs.
+__global__ void __launch_bounds__(kScanThreads) seg_prefix_kernel(const double *x, uint64_t m, double *P,
+                                                                  unsigned long long *last)
 {
+    __shared__ double hs[kScanThreads], hc[kScanThreads];
+    const uint64_t per = (m + kScanThreads - 1) / kScanThreads;
+    const uint64_t b0 = min(m, per * threadIdx.x), b1 = min(m, b0 + per);
+    Neumaier acc;
+    unsigned long long lst = 0;
+    bool any = false;
+    for (uint64_t i = b0; i < b1; ++i) {
+        acc.add(x[i]);
+        if (x[i] > 0.0) {
+            lst = i;
+            any = true;
+        }
+    }
+    if (any) atomicMax(last, lst);
+    hs[threadIdx.x] = acc.s;
+    hc[threadIdx.x] = acc.c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Neumaier run;
+        for (int t = 0; t < kScanThreads; ++t) {
+            const double sv = hs[t], cv = hc[t];
+            hs[t] = run.s;
+            hc[t] = run.c;
+            run.add(sv);
+            run.add(cv);
+        }
+        P[m] = run.value();
+    }
+    __syncthreads();
+    Neumaier r;
+    r.s = hs[threadIdx.x];
+    r.c = hc[threadIdx.x];
+    for (uint64_t i = b0; i < b1; ++i) {
+        P[i] = r.value();
+        r.add(x[i]);
+    }
+}
+
+// Exclusive prefix of the counts cnt[0..m) into off[0..m], one block.
+__global__ void __launch_bounds__(kScanThreads) count_prefix_kernel(const uint32_t *cnt, uint64_t m, uint32_t *off)
+{
+    __shared__ uint32_t hs[kScanThreads];
+    const uint64_t per = (m + kScanThreads - 1) / kScanThreads;
+    const uint64_t b0 = min(m, per * threadIdx.x), b1 = min(m, b0 + per);
+    uint32_t acc = 0;
+    for (uint64_t i = b0; i < b1; ++i) acc += cnt[i];
+    hs[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int t = 0; t < kScanThreads; ++t) {
+            const uint32_t v = hs[t];
+            hs[t] = run;
+            run += v;
+        }
+        off[m] = run;
+    }
+    __syncthreads();
+    uint32_t r = hs[threadIdx.x];
+    for (uint64_t i = b0; i < b1; ++i) {
+        off[i] = r;
+        r += cnt[i];
+    }
+}
+
+// Segment of each shot: the last i with P[i] <= u * total (zero-mass segments
+// are skipped); a target at or past the total, or past the last segment of
+// nonzero probability, takes that segment. Counted per segment.
+__global__ void shot_segment_kernel(const double *u, uint32_t nshots, const double *P, uint64_t nseg,
+                                    const unsigned long long *last, uint32_t *sseg, uint32_t *cnt)
+{
+    const double total = P[nseg];
+    const uint64_t lst = *last;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nshots; k += gridDim.x * blockDim.x) {
+        const double t = __dmul_rn(u[k], total);
+        uint64_t lo = 0, hi = nseg;  // first index with P[i] > t
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi) >> 1;
+            if (P[mid] > t) hi = mid;
+            else lo = mid + 1;
+        }
+        uint64_t i = lo ? lo - 1 : 0;
+        if (!(t < total) || i > lst) i = lst;
+        sseg[k] = uint32_t(i);
+        atomicAdd(&cnt[i], 1u);
+    }
+}
+
+// Place of each shot in the list ordered by segment (order inside a segment
+// is arbitrary: each shot's result depends on its own uniform only).
+__global__ void shot_scatter_kernel(const uint32_t *sseg, uint32_t nshots, const uint32_t *off, uint32_t *cursor,
+                                    uint32_t *sorted)
+{
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nshots; k += gridDim.x * blockDim.x) {
+        const uint32_t sg = sseg[k];
+        sorted[off[sg] + atomicAdd(&cursor[sg], 1u)] = k;
+    }
+}
+
+// One block per segment; segments without shots return at once. Shots of
+// segment s are sorted[off[s] .. off[s+1]); the target inside the segment is
+// u * total - P[s].
+template <typename R>
+__global__ void __launch_bounds__(kThreadsS) seg_search_kernel(const R *__restrict__ a, uint64_t N, const double *P,
+                                                               uint64_t nseg, const uint32_t *off,
+                                                               const uint32_t *sorted, const double *u, uint64_t *out)
+{
+    const uint64_t sg = blockIdx.x;
+    const uint32_t j0 = off[sg], j1 = off[sg + 1];
+    if (j0 == j1) return;
     __shared__ double cdf[kSeg];
-    const uint64_t s0 = segments[blockIdx.x] * kSeg;
+    const uint64_t s0 = sg * kSeg;
     const int len = int(N - s0 < uint64_t(kSeg) ? N - s0 : uint64_t(kSeg));
     for (int l = threadIdx.x; l < kSeg; l += kThreadsS) cdf[l] = l < len ? prob(a, s0 + l) : 0.0;
     __syncthreads();
     // inclusive scan (Hillis-Steele) in FP64
-    for (int off = 1; off < kSeg; off <<= 1) {
+    for (int o = 1; o < kSeg; o <<= 1) {
         double v[kSeg / kThreadsS];
 #pragma unroll
         for (int k = 0; k < kSeg / kThreadsS; ++k) {
             const int l = threadIdx.x + k * kThreadsS;
-            v[k] = l >= off ? cdf[l - off] : 0.0;
+            v[k] = l >= o ? cdf[l - o] : 0.0;
         }
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < kSeg / kThreadsS; ++k) cdf[threadIdx.x + k * kThreadsS] += v[k];
         __syncthreads();
     }
-    const double segtot = cdf[len - 1];
-    for (uint32_t k = first[blockIdx.x] + threadIdx.x; k < first[blockIdx.x + 1]; k += kThreadsS) {
-        const double t = local[k];
+    const double segtot = cdf[len - 1], total = P[nseg], base = P[sg];
+    for (uint32_t j = j0 + threadIdx.x; j < j1; j += kThreadsS) {
+        const uint32_t k = sorted[j];
+        const double t = __dsub_rn(__dmul_rn(u[k], total), base);
         // smallest l with cdf[l] > t; a target at or past the segment's total (rounding
         // at u -> 1) takes the last outcome with nonzero probability
         const bool past = !(t < segtot);
@@ -106,75 +222,46 @@ template <typename R> qv_status sample_impl(qv_state *s, const double *u, size_t
 {
     const uint64_t N = dim(s);
     const uint64_t nseg = (N + kSeg - 1) / kSeg;
-    QV_TRY(ensure_scratch(s, nseg * sizeof(double)));
-    double *seg = static_cast<double *>(s->scratch.ptr);
+    const uint32_t ns = uint32_t(nshots);
+    auto up16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+    // scratch: seg, P, last, cnt (then the scatter cursor), off, u, sseg, sorted, out
+    const size_t b_seg = up16(nseg * sizeof(double)), b_P = up16((nseg + 1) * sizeof(double)), b_last = 16;
+    const size_t b_cnt = up16((nseg + 1) * sizeof(uint32_t)), b_u = up16(nshots * sizeof(double));
+    const size_t b_idx = up16(nshots * sizeof(uint32_t)), b_out = up16(nshots * sizeof(uint64_t));
+    QV_TRY(ensure_scratch(s, b_seg + b_P + b_last + 2 * b_cnt + b_u + 2 * b_idx + b_out));
+    char *p = static_cast<char *>(s->scratch.ptr);
+    double *seg = reinterpret_cast<double *>(p);
+    double *P = reinterpret_cast<double *>(p += b_seg);
+    unsigned long long *last = reinterpret_cast<unsigned long long *>(p += b_P);
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(p += b_last);
+    uint32_t *off = reinterpret_cast<uint32_t *>(p += b_cnt);
+    double *du = reinterpret_cast<double *>(p += b_cnt);
+    uint32_t *sseg = reinterpret_cast<uint32_t *>(p += b_u);
+    uint32_t *sorted = reinterpret_cast<uint32_t *>(p += b_idx);
+    uint64_t *dout = reinterpret_cast<uint64_t *>(p += b_idx);
+    const R *a = static_cast<const R *>(s->amp);
+
     prof_bytes(s, QV_K_REDUCE, double(N) * 2 * sizeof(R));
-    QV_LAUNCH(s, QV_K_REDUCE, seg_prob_kernel<R><<<unsigned(nseg), kThreadsS, 0, s->stream>>>(
-                                  static_cast<const R *>(s->amp), N, seg));
-    std::vector<double> hseg(nseg);
-    QV_TRY(copy_d2h(s, hseg.data(), seg, nseg * sizeof(double)));
+    QV_LAUNCH(s, QV_K_REDUCE, seg_prob_kernel<R><<<unsigned(nseg), kThreadsS, 0, s->stream>>>(a, N, seg));
+    QV_CUDA(cudaMemsetAsync(last, 0, sizeof(unsigned long long), s->stream));
+    QV_LAUNCH(s, QV_K_REDUCE, seg_prefix_kernel<<<1, kScanThreads, 0, s->stream>>>(seg, nseg, P, last));
+    double total = 0;
+    QV_TRY(copy_d2h(s, &total, P + nseg, sizeof(double)));
     QV_TRY(sync_and_check(s));
-    // exclusive prefix P[i] and total (compensated running sum)
-    std::vector<double> P(nseg + 1);
-    Neumaier run;
-    for (uint64_t i = 0; i < nseg; ++i) {
-        P[i] = run.value();
-        run.add(hseg[i]);
-    }
-    P[nseg] = run.value();
-    const double total = P[nseg];
     if (!(total > 0)) return fail(QV_ERR_ARG, "the state has zero norm");
-    // shots per segment, in segment order
-    std::vector<uint64_t> sseg(nshots);
-    uint64_t last = nseg - 1;  // last segment with nonzero probability
-    while (last > 0 && !(hseg[last] > 0.0)) --last;
-    for (size_t k = 0; k < nshots; ++k) {
-        const double t = u[k] * total;
-        // P[i] <= t < P[i + 1]; upper_bound skips segments of zero mass
-        uint64_t i = uint64_t(std::upper_bound(P.begin(), P.begin() + nseg, t) - P.begin());
-        i = i ? i - 1 : 0;
-        if (!(t < total) || i > last) i = last;
-        sseg[k] = i;
-    }
-    // shots in segment order (counting sort over the segments)
-    std::vector<uint32_t> count(nseg + 1, 0), order(nshots);
-    for (size_t k = 0; k < nshots; ++k) ++count[sseg[k] + 1];
-    for (uint64_t i = 0; i < nseg; ++i) count[i + 1] += count[i];
-    for (size_t k = 0; k < nshots; ++k) order[count[sseg[k]]++] = uint32_t(k);
-    std::vector<uint64_t> segs;
-    std::vector<uint32_t> first;
-    std::vector<double> local(nshots);
-    for (size_t j = 0; j < nshots; ++j) {
-        const uint32_t k = order[j];
-        if (segs.empty() || segs.back() != sseg[k]) {
-            segs.push_back(sseg[k]);
-            first.push_back(uint32_t(j));
-        }
-        local[j] = u[k] * total - P[sseg[k]];
-    }
-    first.push_back(uint32_t(nshots));
-    // device buffers: segments, first, local, result
-    const size_t b_seg = segs.size() * sizeof(uint64_t), b_first = first.size() * sizeof(uint32_t);
-    const size_t b_loc = nshots * sizeof(double), b_out = nshots * sizeof(uint64_t);
-    const size_t a8 = [](size_t x) { return (x + 15) & ~size_t(15); }(b_seg);
-    const size_t a_first = (b_first + 15) & ~size_t(15), a_loc = (b_loc + 15) & ~size_t(15);
-    QV_TRY(ensure_scratch(s, a8 + a_first + a_loc + b_out));
-    char *base = static_cast<char *>(s->scratch.ptr);
-    uint64_t *d_seg = reinterpret_cast<uint64_t *>(base);
-    uint32_t *d_first = reinterpret_cast<uint32_t *>(base + a8);
-    double *d_loc = reinterpret_cast<double *>(base + a8 + a_first);
-    uint64_t *d_out = reinterpret_cast<uint64_t *>(base + a8 + a_first + a_loc);
-    QV_TRY(copy_h2d(s, d_seg, segs.data(), b_seg));
-    QV_TRY(copy_h2d(s, d_first, first.data(), b_first));
-    QV_TRY(copy_h2d(s, d_loc, local.data(), b_loc));
-    prof_bytes(s, QV_K_REDUCE, double(segs.size()) * kSeg * 2 * sizeof(R));
-    QV_LAUNCH(s, QV_K_REDUCE, seg_search_kernel<R><<<unsigned(segs.size()), kThreadsS, 0, s->stream>>>(
-                                  static_cast<const R *>(s->amp), N, d_seg, d_first, d_loc, d_out));
-    std::vector<uint64_t> res(nshots);
-    QV_TRY(copy_d2h(s, res.data(), d_out, b_out));
-    QV_TRY(sync_and_check(s));
-    for (size_t j = 0; j < nshots; ++j) out[order[j]] = res[j];
-    return QV_OK;
+    QV_TRY(copy_h2d(s, du, u, nshots * sizeof(double)));
+    QV_CUDA(cudaMemsetAsync(cnt, 0, (nseg + 1) * sizeof(uint32_t), s->stream));
+    const unsigned grid = unsigned(std::min<size_t>((nshots + 255) / 256, size_t(s->num_sms) * 8));
+    QV_LAUNCH(s, QV_K_REDUCE,
+              shot_segment_kernel<<<grid, 256, 0, s->stream>>>(du, ns, P, nseg, last, sseg, cnt));
+    QV_LAUNCH(s, QV_K_REDUCE, count_prefix_kernel<<<1, kScanThreads, 0, s->stream>>>(cnt, nseg, off));
+    QV_CUDA(cudaMemsetAsync(cnt, 0, (nseg + 1) * sizeof(uint32_t), s->stream));
+    QV_LAUNCH(s, QV_K_REDUCE, shot_scatter_kernel<<<grid, 256, 0, s->stream>>>(sseg, ns, off, cnt, sorted));
+    prof_bytes(s, QV_K_REDUCE, double(N) * 2 * sizeof(R));
+    QV_LAUNCH(s, QV_K_REDUCE,
+              seg_search_kernel<R><<<unsigned(nseg), kThreadsS, 0, s->stream>>>(a, N, P, nseg, off, sorted, du, dout));
+    QV_TRY(copy_d2h(s, out, dout, nshots * sizeof(uint64_t)));
+    return sync_and_check(s);
 }
 
 template <typename R> qv_status gather_impl(qv_state *s, const uint64_t *idx, size_t k, void *host)
