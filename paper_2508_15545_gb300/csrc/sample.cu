@@ -13,8 +13,9 @@
 //     counted per segment;
 //  4. one block: exclusive prefix of the counts; then each shot's place in the
 //     shot list ordered by segment (counting sort);
-//  5. per segment holding shots: an inclusive FP64 scan of its probabilities in
-//     shared memory and a binary search per shot.
+//  5. per segment holding shots: FP64 sums of runs of its probabilities in shared
+//     memory, a prefix over the runs, and per shot a binary search over the runs
+//     and a short sequential search inside one.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -36,26 +37,21 @@ template <typename R> __device__ __forceinline__ double prob(const R *a, uint64_
     return re * re + im * im;
 }
 
-// seg[s] = sum of the probabilities of segment s (FP64, compensated)
+// seg[s] = sum of the probabilities of segment s (FP64, compensated across threads)
 template <typename R>
 __global__ void __launch_bounds__(kThreadsS) seg_prob_kernel(const R *__restrict__ a, uint64_t N, double *seg)
 {
     const uint64_t s0 = uint64_t(blockIdx.x) * kSeg;
     const uint64_t s1 = min(N, s0 + kSeg);
-    Neumaier acc;
-    for (uint64_t i = s0 + threadIdx.x; i < s1; i += kThreadsS) acc.add(prob(a, i));
-    __shared__ double hs[kThreadsS], cs[kThreadsS];
-    hs[threadIdx.x] = acc.s;
-    cs[threadIdx.x] = acc.c;
+    double acc = 0;  // 16 nonnegative terms per thread: plain FP64 is enough there
+    for (uint64_t i = s0 + threadIdx.x; i < s1; i += kThreadsS) acc += prob(a, i);
+    __shared__ double hs[kThreadsS];
+    hs[threadIdx.x] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
         Neumaier t;
-        double c = 0;
-        for (int k = 0; k < kThreadsS; ++k) {
-            t.add(hs[k]);
-            c += cs[k];
-        }
-        seg[blockIdx.x] = t.value() + c;
+        for (int k = 0; k < kThreadsS; ++k) t.add(hs[k]);
+        seg[blockIdx.x] = t.value();
     }
 }
 
@@ -166,47 +162,72 @@ __global__ void shot_scatter_kernel(const uint32_t *sseg, uint32_t nshots, const
 
 // One block per segment; segments without shots return at once. Shots of
 // segment s are sorted[off[s] .. off[s+1]); the target inside the segment is
-// u * total - P[s].
+// t = u * total - P[s]. Thread j sums the run of kRun probabilities
+// [j kRun, (j + 1) kRun); cs[] is the inclusive prefix over the runs. A shot
+// takes the first run whose prefix exceeds t, then the first outcome inside it
+// whose running sum exceeds t; a target at or past the segment's total (rounding
+// at u -> 1) takes the last outcome with nonzero probability.
 template <typename R>
 __global__ void __launch_bounds__(kThreadsS) seg_search_kernel(const R *__restrict__ a, uint64_t N, const double *P,
                                                                uint64_t nseg, const uint32_t *off,
                                                                const uint32_t *sorted, const double *u, uint64_t *out)
 {
+    constexpr int kRun = kSeg / kThreadsS;
     const uint64_t sg = blockIdx.x;
     const uint32_t j0 = off[sg], j1 = off[sg + 1];
     if (j0 == j1) return;
-    __shared__ double cdf[kSeg];
+    __shared__ double pr[kSeg];
+    __shared__ double cs[kThreadsS + 1];
+    __shared__ int lastnz;
     const uint64_t s0 = sg * kSeg;
     const int len = int(N - s0 < uint64_t(kSeg) ? N - s0 : uint64_t(kSeg));
-    for (int l = threadIdx.x; l < kSeg; l += kThreadsS) cdf[l] = l < len ? prob(a, s0 + l) : 0.0;
+    if (threadIdx.x == 0) lastnz = 0;
+    for (int l = threadIdx.x; l < kSeg; l += kThreadsS) pr[l] = l < len ? prob(a, s0 + l) : 0.0;
     __syncthreads();
-    // inclusive scan (Hillis-Steele) in FP64
-    for (int o = 1; o < kSeg; o <<= 1) {
-        double v[kSeg / kThreadsS];
-#pragma unroll
-        for (int k = 0; k < kSeg / kThreadsS; ++k) {
-            const int l = threadIdx.x + k * kThreadsS;
-            v[k] = l >= o ? cdf[l - o] : 0.0;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < kSeg / kThreadsS; ++k) cdf[threadIdx.x + k * kThreadsS] += v[k];
-        __syncthreads();
+    double acc = 0;
+    int lz = -1;
+    for (int i = 0; i < kRun; ++i) {  // rotated start: the threads of a warp hit distinct banks
+        const int x = int(threadIdx.x) * kRun + ((i + int(threadIdx.x)) & (kRun - 1));
+        const double v = pr[x];
+        acc += v;
+        if (v > 0.0) lz = max(lz, x);
     }
-    const double segtot = cdf[len - 1], total = P[nseg], base = P[sg];
+    cs[threadIdx.x + 1] = acc;
+    if (lz >= 0) atomicMax(&lastnz, lz);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cs[0] = 0.0;
+        for (int j = 1; j <= kThreadsS; ++j) cs[j] += cs[j - 1];
+    }
+    __syncthreads();
+    const double segtot = cs[kThreadsS], total = P[nseg], base = P[sg];
     for (uint32_t j = j0 + threadIdx.x; j < j1; j += kThreadsS) {
         const uint32_t k = sorted[j];
         const double t = __dsub_rn(__dmul_rn(u[k], total), base);
-        // smallest l with cdf[l] > t; a target at or past the segment's total (rounding
-        // at u -> 1) takes the last outcome with nonzero probability
-        const bool past = !(t < segtot);
-        int lo = 0, hi = len - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (past ? cdf[mid] >= segtot : cdf[mid] > t) hi = mid;
-            else lo = mid + 1;
+        int l = lastnz;
+        if (t < segtot) {
+            int lo = 0, hi = kThreadsS - 1;  // first run r with cs[r + 1] > t
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (cs[mid + 1] > t) hi = mid;
+                else lo = mid + 1;
+            }
+            double run = cs[lo];
+            int last_in_run = -1;
+            l = -1;
+            for (int i = 0; i < kRun; ++i) {
+                const int x = lo * kRun + i;
+                if (pr[x] > 0.0) last_in_run = x;
+                run += pr[x];
+                if (run > t) {
+                    l = x;
+                    break;
+                }
+            }
+            // the running sum can round to at most t inside the run: its last outcome
+            if (l < 0) l = last_in_run >= 0 ? last_in_run : lastnz;
         }
-        out[k] = s0 + uint64_t(lo);
+        out[k] = s0 + uint64_t(l);
     }
 }
 
