@@ -3,8 +3,10 @@
 //
 // Sampling is inverse-CDF sampling of the Born distribution p_i = |a_i|^2 /
 // sum |a|^2: for a uniform u in [0, 1), the outcome is the smallest i whose
-// cumulative probability exceeds u. The uniforms are inputs. Probabilities and
-// all sums are FP64 (a squared FP32 component is exact in FP64). Every step
+// cumulative probability exceeds u. The uniforms are inputs. Single
+// probabilities are FP64 (a squared FP32 component is exact in FP64); sums of
+// complex64 probabilities over runs of amplitudes are two-float sums of exact
+// squares (see Slot), and everything from segment totals on is FP64. Every step
 // runs on the device:
 //  1. per segment of kSeg amplitudes: its probability sum (one read of the state);
 //  2. one block: compensated exclusive prefix P over the segments (P[nseg] = total)
@@ -31,26 +33,100 @@ constexpr int kSeg = 1 << kSegBitsS;
 constexpr int kThreadsS = 256;
 constexpr int kScanThreads = 1024;  // one block for the prefix over segments
 
-template <typename R> __device__ __forceinline__ double prob(const R *a, uint64_t i)
-{
-    const double re = a[2 * i], im = a[2 * i + 1];
-    return re * re + im * im;
-}
+// Per-amplitude slot of a segment in shared memory and the sums over runs of
+// them. complex64: the raw FP32 components; a square of an FP32 value is
+// exact as an FP32 product plus its FMA error term, and run sums are kept as
+// two FP32 values (Dekker's two-sum), about 2^-44 relative, then one FP64
+// conversion per run, which spares GB300's slow FP64 pipe. Single
+// probabilities are FP64 (exact squares), as in the oracle. complex128: FP64
+// probabilities and plain FP64 sums.
+template <typename R> struct Slot;
+template <> struct Slot<float> {
+    using T = float2;
+    static __device__ __forceinline__ T load(const float *a, uint64_t i) { return make_float2(a[2 * i], a[2 * i + 1]); }
+    static __device__ __forceinline__ T zero() { return make_float2(0.f, 0.f); }
+    static __device__ __forceinline__ double p(T v)
+    {
+        const double re = v.x, im = v.y;
+        return re * re + im * im;
+    }
+    static __device__ __forceinline__ bool nonzero(T v) { return v.x != 0.f || v.y != 0.f; }
+    struct Acc {
+        float h = 0.f, l = 0.f;
+        __device__ __forceinline__ void two_sum(float x)
+        {
+            const float s = __fadd_rn(h, x), bb = __fsub_rn(s, h);
+            l = __fadd_rn(l, __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(x, bb)));
+            h = s;
+        }
+        __device__ __forceinline__ void square(float x)
+        {
+            const float q = __fmul_rn(x, x);
+            two_sum(q);
+            l = __fadd_rn(l, fmaf(x, x, -q));
+        }
+        __device__ __forceinline__ void add(T v)
+        {
+            square(v.x);
+            square(v.y);
+        }
+        __device__ __forceinline__ void merge(const Acc &o)
+        {
+            two_sum(o.h);
+            l = __fadd_rn(l, o.l);
+        }
+        __device__ __forceinline__ Acc shfl_xor(int m) const
+        {
+            Acc o;
+            o.h = __shfl_xor_sync(0xffffffffu, h, m);
+            o.l = __shfl_xor_sync(0xffffffffu, l, m);
+            return o;
+        }
+        __device__ __forceinline__ double value() const { return double(h) + double(l); }
+    };
+};
+template <> struct Slot<double> {
+    using T = double;
+    static __device__ __forceinline__ T load(const double *a, uint64_t i)
+    {
+        const double re = a[2 * i], im = a[2 * i + 1];
+        return re * re + im * im;
+    }
+    static __device__ __forceinline__ T zero() { return 0.0; }
+    static __device__ __forceinline__ double p(T v) { return v; }
+    static __device__ __forceinline__ bool nonzero(T v) { return v > 0.0; }
+    struct Acc {
+        double s = 0.0;
+        __device__ __forceinline__ void add(T v) { s += v; }
+        __device__ __forceinline__ void merge(const Acc &o) { s += o.s; }
+        __device__ __forceinline__ Acc shfl_xor(int m) const
+        {
+            Acc o;
+            o.s = __shfl_xor_sync(0xffffffffu, s, m);
+            return o;
+        }
+        __device__ __forceinline__ double value() const { return s; }
+    };
+};
 
-// seg[s] = sum of the probabilities of segment s (FP64, compensated across threads)
+// seg[s] = sum of the probabilities of segment s
 template <typename R>
 __global__ void __launch_bounds__(kThreadsS) seg_prob_kernel(const R *__restrict__ a, uint64_t N, double *seg)
 {
     const uint64_t s0 = uint64_t(blockIdx.x) * kSeg;
     const uint64_t s1 = min(N, s0 + kSeg);
-    double acc = 0;  // 16 nonnegative terms per thread: plain FP64 is enough there
-    for (uint64_t i = s0 + threadIdx.x; i < s1; i += kThreadsS) acc += prob(a, i);
-    __shared__ double hs[kThreadsS];
-    hs[threadIdx.x] = acc;
+    using Acc = typename Slot<R>::Acc;
+    Acc acc;
+    for (uint64_t i = s0 + threadIdx.x; i < s1; i += kThreadsS) acc.add(Slot<R>::load(a, i));
+    // combine across the block with shuffles in the same arithmetic: a serial
+    // FP64 loop in one thread would hold the FP64 pipe for whole warps
+    for (int m = 16; m > 0; m >>= 1) acc.merge(acc.shfl_xor(m));
+    __shared__ Acc ws[kThreadsS / 32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        Neumaier t;
-        for (int k = 0; k < kThreadsS; ++k) t.add(hs[k]);
+        Acc t = ws[0];
+        for (int w = 1; w < kThreadsS / 32; ++w) t.merge(ws[w]);
         seg[blockIdx.x] = t.value();
     }
 }
@@ -176,29 +252,38 @@ __global__ void __launch_bounds__(kThreadsS) seg_search_kernel(const R *__restri
     const uint64_t sg = blockIdx.x;
     const uint32_t j0 = off[sg], j1 = off[sg + 1];
     if (j0 == j1) return;
-    __shared__ double pr[kSeg];
+    using S = Slot<R>;
+    __shared__ typename S::T el[kSeg];
     __shared__ double cs[kThreadsS + 1];
     __shared__ int lastnz;
     const uint64_t s0 = sg * kSeg;
     const int len = int(N - s0 < uint64_t(kSeg) ? N - s0 : uint64_t(kSeg));
     if (threadIdx.x == 0) lastnz = 0;
-    for (int l = threadIdx.x; l < kSeg; l += kThreadsS) pr[l] = l < len ? prob(a, s0 + l) : 0.0;
+    for (int l = threadIdx.x; l < kSeg; l += kThreadsS) el[l] = l < len ? S::load(a, s0 + l) : S::zero();
     __syncthreads();
-    double acc = 0;
+    typename S::Acc acc;
     int lz = -1;
     for (int i = 0; i < kRun; ++i) {  // rotated start: the threads of a warp hit distinct banks
         const int x = int(threadIdx.x) * kRun + ((i + int(threadIdx.x)) & (kRun - 1));
-        const double v = pr[x];
-        acc += v;
-        if (v > 0.0) lz = max(lz, x);
+        const typename S::T v = el[x];
+        acc.add(v);
+        if (S::nonzero(v)) lz = max(lz, x);
     }
-    cs[threadIdx.x + 1] = acc;
     if (lz >= 0) atomicMax(&lastnz, lz);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        cs[0] = 0.0;
-        for (int j = 1; j <= kThreadsS; ++j) cs[j] += cs[j - 1];
+    // inclusive prefix over the runs: within each warp by shuffles, then the warp offsets
+    __shared__ double wtot[kThreadsS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double v = acc.value();
+    for (int d = 1; d < 32; d <<= 1) {
+        const double o = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += o;
     }
+    if (lane == 31) wtot[warp] = v;
+    __syncthreads();
+    double woff = 0.0;
+    for (int w = 0; w < warp; ++w) woff += wtot[w];
+    cs[threadIdx.x + 1] = woff + v;
+    if (threadIdx.x == 0) cs[0] = 0.0;
     __syncthreads();
     const double segtot = cs[kThreadsS], total = P[nseg], base = P[sg];
     for (uint32_t j = j0 + threadIdx.x; j < j1; j += kThreadsS) {
@@ -217,8 +302,8 @@ __global__ void __launch_bounds__(kThreadsS) seg_search_kernel(const R *__restri
             l = -1;
             for (int i = 0; i < kRun; ++i) {
                 const int x = lo * kRun + i;
-                if (pr[x] > 0.0) last_in_run = x;
-                run += pr[x];
+                if (S::nonzero(el[x])) last_in_run = x;
+                run += S::p(el[x]);
                 if (run > t) {
                     l = x;
                     break;
