@@ -140,6 +140,24 @@ __device__ __forceinline__ void two_sum(R a, R b, R &s, R &e)
     e = (a - (s - bb)) + (b - bb);
 }
 
+// re^2 + im^2 = h + l exactly up to the rounding of l: each square as its
+// rounded product plus the FMA error term, the two high parts by two-sum.
+// The products use explicit round-to-nearest so they are not contracted.
+__device__ __forceinline__ void exact_norm2(float re, float im, float &h, float &l)
+{
+    const float hr = __fmul_rn(re, re), hi = __fmul_rn(im, im);
+    float e;
+    two_sum(hr, hi, h, e);
+    l = e + (fmaf(re, re, -hr) + fmaf(im, im, -hi));
+}
+__device__ __forceinline__ void exact_norm2(double re, double im, double &h, double &l)
+{
+    const double hr = __dmul_rn(re, re), hi = __dmul_rn(im, im);
+    double e;
+    two_sum(hr, hi, h, e);
+    l = e + (fma(re, re, -hr) + fma(im, im, -hi));
+}
+
 // Running compensated sum in precision R: hi + lo carries the exact sum of
 // everything added so far up to the rounding of lo.
 template <typename R> struct CompSum {
@@ -150,6 +168,14 @@ template <typename R> struct CompSum {
         two_sum(hi, x, s, e);
         hi = s;
         lo += e;
+    }
+    // adds another running sum (two-sum of the high parts, low parts added)
+    __device__ __forceinline__ void merge(R ohi, R olo)
+    {
+        R s, e;
+        two_sum(hi, ohi, s, e);
+        hi = s;
+        lo += e + olo;
     }
     __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
 };

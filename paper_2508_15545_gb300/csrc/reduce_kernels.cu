@@ -2,10 +2,13 @@
 // expectation values. Not part of the paper (which reports no observables);
 // they read the state once and never write it.
 //
-// Precision: |a|^2 and short runs inside a thread are summed in the state's
-// precision with error-free two-sum compensation (hi + lo), so a thread's
-// partial carries about twice the working precision. Partials are combined in
-// FP64 (shuffle trees inside a block, Neumaier-compensated sums across blocks).
+// Precision: |a|^2 is formed exactly as hi + lo (each square as its rounded
+// product plus the FMA error term) in the norm and Z sums, and short runs
+// inside a thread are summed in the state's precision with error-free two-sum
+// compensation, so a thread's partial carries about twice the working
+// precision. complex64 partials are merged across a block in the same
+// two-float arithmetic and converted to FP64 once per block; complex128 ones
+// by FP64 shuffle trees. Blocks are combined with Neumaier-compensated FP64 sums.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -51,6 +54,45 @@ template <int V> __device__ void block_sum(double (&x)[V], double (*smem)[V])
     }
 }
 
+// Combines V running sums over the block and writes their values to out[0..V).
+// complex64: in FP32 two-sum arithmetic with shuffles, converted to FP64 once
+// per value (GB300's FP64 pipe is about 1/64 of FP32: FP64 shuffle trees over
+// every block cost more than reading the state). complex128: FP64 trees.
+template <typename R, int V> __device__ void block_merge(CompSum<R> (&x)[V], double *out)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if constexpr (sizeof(R) == 4) {
+        __shared__ R sh_hi[kThreads / 32][V], sh_lo[kThreads / 32][V];
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                x[v].merge(__shfl_xor_sync(0xffffffffu, x[v].hi, o), __shfl_xor_sync(0xffffffffu, x[v].lo, o));
+        if (lane == 0)
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                sh_hi[warp][v] = x[v].hi;
+                sh_lo[warp][v] = x[v].lo;
+            }
+        __syncthreads();
+        if (threadIdx.x < V) {
+            CompSum<R> s;
+            s.hi = sh_hi[0][threadIdx.x];
+            s.lo = sh_lo[0][threadIdx.x];
+            for (int w = 1; w < kThreads / 32; ++w) s.merge(sh_hi[w][threadIdx.x], sh_lo[w][threadIdx.x]);
+            out[threadIdx.x] = s.value();
+        }
+    } else {
+        __shared__ double smem[kThreads / 32][V];
+        double y[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) y[v] = x[v].value();
+        block_sum<V>(y, smem);
+        if (threadIdx.x == 0)
+            for (int v = 0; v < V; ++v) out[v] = y[v];
+    }
+}
+
 // ---------------------------------------------------------------- small states
 // One block: out[0] = sum |a|^2, out[1+q] = sum_{bit q set} |a|^2.
 template <typename R> __global__ void __launch_bounds__(kThreads) zsum_small_kernel(const R *amp, int n, double *out)
@@ -82,7 +124,6 @@ template <typename R> __global__ void __launch_bounds__(kThreads) zsum_seg_kerne
     constexpr int W = Traits<R>::W, LOGW = Traits<R>::LOGW;
     constexpr int TB = 8;                         // thread bits
     constexpr int VB = kSegBits - LOGW - TB;      // loop bits
-    __shared__ double smem[kThreads / 32][kParts];
     CompSum<R> tot, eb[LOGW], vb[VB];
     const uint64_t seg = uint64_t(blockIdx.x) << kSegBits;
     const int t = threadIdx.x;
@@ -90,37 +131,34 @@ template <typename R> __global__ void __launch_bounds__(kThreads) zsum_seg_kerne
     for (int v = 0; v < (1 << VB); ++v) {
         AmpGroup<R, W> a;
         load_group(amp, seg + (uint64_t(t) << LOGW) + (uint64_t(v) << (LOGW + TB)), a);
-        R p[W];
+        R ph[W], pl[W];  // |a|^2 exactly as ph + pl (up to the rounding of pl)
 #pragma unroll
-        for (int e = 0; e < W; ++e) p[e] = a.re[e] * a.re[e] + a.im[e] * a.im[e];
-        R w = 0;
+        for (int e = 0; e < W; ++e) exact_norm2(a.re[e], a.im[e], ph[e], pl[e]);
+        CompSum<R> w;
 #pragma unroll
-        for (int e = 0; e < W; ++e) w += p[e];
-        tot.add(w);
+        for (int e = 0; e < W; ++e) w.merge(ph[e], pl[e]);
+        tot.merge(w.hi, w.lo);
 #pragma unroll
         for (int k = 0; k < LOGW; ++k) {
-            R s = 0;
+            CompSum<R> sk;
 #pragma unroll
             for (int e = 0; e < W; ++e)
-                if ((e >> k) & 1) s += p[e];
-            eb[k].add(s);
+                if ((e >> k) & 1) sk.merge(ph[e], pl[e]);
+            eb[k].merge(sk.hi, sk.lo);
         }
 #pragma unroll
         for (int k = 0; k < VB; ++k)
-            if ((v >> k) & 1) vb[k].add(w);
+            if ((v >> k) & 1) vb[k].merge(w.hi, w.lo);
     }
-    double x[kParts];
-    const double T = tot.value();
-    x[0] = T;
+    CompSum<R> x[kParts];
+    x[0] = tot;
 #pragma unroll
-    for (int k = 0; k < LOGW; ++k) x[1 + k] = eb[k].value();
+    for (int k = 0; k < LOGW; ++k) x[1 + k] = eb[k];
 #pragma unroll
-    for (int k = 0; k < TB; ++k) x[1 + LOGW + k] = ((t >> k) & 1) ? T : 0.0;
+    for (int k = 0; k < TB; ++k) x[1 + LOGW + k] = ((t >> k) & 1) ? tot : CompSum<R>();
 #pragma unroll
-    for (int k = 0; k < VB; ++k) x[1 + LOGW + TB + k] = vb[k].value();
-    block_sum<kParts>(x, smem);
-    if (t == 0)
-        for (int v = 0; v < kParts; ++v) part[uint64_t(blockIdx.x) * kParts + v] = x[v];
+    for (int k = 0; k < VB; ++k) x[1 + LOGW + TB + k] = vb[k];
+    block_merge<R, kParts>(x, part + uint64_t(blockIdx.x) * kParts);
 }
 
 // Output o = 0: total; o = 1 + q: S_q. For q < 14 sum column 1+q of the
