@@ -117,6 +117,26 @@ def test_reductions(qvlib, orc, cuda, dtype, n):
     qv.qv_destroy(h)
 
 
+@pytest.mark.parametrize("n", [14, 17])
+def test_norm_and_z_sums_exact_squares(qvlib, orc, cuda, n):
+    """complex64 norm and Z sums on a state whose magnitudes span six decades
+    (not normalised): the squares are formed exactly (rounded product plus its
+    FMA error term) and merged in two-float arithmetic, so they agree with the
+    oracle on the stored amplitudes to about 1e-13 relative, where rounded FP32
+    squares would leave errors near 1e-8."""
+    qv = qvlib
+    psi = W.random_state(n, 900 + n, normalize=False)
+    scale = 10.0 ** (3.0 * W.SplitMix64(n + 1).uniform(1 << n) - 1.5)
+    psi = (psi * scale).astype(np.complex64)
+    h = new_state(qv, n, 0, psi)
+    ref = qv.qv_get_state(h).astype(np.complex128)
+    want = orc.norm2(ref)
+    assert abs(qv.qv_norm2(h) - want) <= 1e-12 * want
+    ez, _ = qv.qv_expect_z(h)
+    assert np.max(np.abs(ez - orc.expect_z(ref))) <= 1e-12 * want
+    qv.qv_destroy(h)
+
+
 @pytest.mark.parametrize("n", [2, 5, 10])
 def test_permute_qubits(qvlib, orc, cuda, n):
     qv = qvlib
