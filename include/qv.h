@@ -390,6 +390,13 @@ qv_status qv_batch_run(qv_batch *b, double *expvals);
 
 qv_status qv_batch_destroy(qv_batch *b);
 
+/* One-shot batch: qv_batch_create, one qv_batch_run and qv_batch_destroy in a
+ * single call, with the same arguments and rules (expvals[count] may be NULL).
+ * For repeated runs of the same circuits keep a qv_batch instead: creating it
+ * plans, compiles and captures the graph. */
+qv_status qv_apply_batch(const qv_batch_item *items, size_t count, const qv_pauli_term *H, size_t nt,
+                         const qv_plan_opts *opts, double *expvals);
+
 /* Waits for the handle's stream and reports device-side failures: kernels
  * whose waits are bounded (the compiled fused passes' tile copies, the batch
  * dependencies) write a status word instead of hanging; this call (and every

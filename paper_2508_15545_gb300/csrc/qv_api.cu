@@ -530,6 +530,16 @@ qv_status qv_batch_destroy(qv_batch *b)
     return QV_OK;
 }
 
+qv_status qv_apply_batch(const qv_batch_item *items, size_t count, const qv_pauli_term *H, size_t nt,
+                         const qv_plan_opts *opts, double *expvals)
+{
+    qv_batch *b = nullptr;
+    QV_TRY(qv_batch_create(items, count, H, nt, opts, &b));
+    const qv_status st = qv_batch_run(b, expvals);
+    batch_release(b);
+    return st;
+}
+
 qv_status qv_verify_qft(qv_state *s, uint64_t j, double *dist)
 {
     CHECK_HANDLE(s);

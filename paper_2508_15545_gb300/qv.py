@@ -108,6 +108,8 @@ def _load():
                             ctypes.c_size_t, ctypes.POINTER(qv_plan_opts), ctypes.POINTER(ctypes.c_void_p)],
         "qv_batch_run": [ctypes.c_void_p, P],
         "qv_batch_destroy": [ctypes.c_void_p],
+        "qv_apply_batch": [ctypes.POINTER(qv_batch_item), ctypes.c_size_t, ctypes.POINTER(qv_pauli_term),
+                           ctypes.c_size_t, ctypes.POINTER(qv_plan_opts), P],
         "qv_verify_qft": [_H, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)],
         "qv_sync": [_H],
         "qv_default_tile_bits": [ctypes.c_int, ctypes.c_int, ctypes.c_int32],
@@ -356,6 +358,24 @@ def qv_autotune(h: int, gates, flags: int = 0) -> int:
     best = ctypes.c_int32()
     _check(lib.qv_autotune(h, arr, ng, ctypes.byref(opts), ctypes.byref(best)))
     return best.value
+
+
+def qv_apply_batch(items, terms=None, tile_bits: int = 0, flags: int = 0) -> np.ndarray:
+    """One-shot batch (qv_apply_batch): runs every (state, circuit) pair from
+    |0...0> and returns <H> per state (zeros without terms)."""
+    count = len(items)
+    arrs = [_gate_array(g) for _, g in items]
+    c_items = (qv_batch_item * max(1, count))()
+    for k, ((h, _), (arr, ng)) in enumerate(zip(items, arrs)):
+        c_items[k].state = h
+        c_items[k].gates = ctypes.cast(arr, ctypes.POINTER(qv_gate))
+        c_items[k].ngates = ng
+    terms = list(terms or [])
+    opts = plan_opts(QV_MODE_FUSED, tile_bits, flags)
+    out = np.zeros(max(1, count))
+    _check(lib.qv_apply_batch(c_items, count, terms_to_c(terms), len(terms), ctypes.byref(opts),
+                              out.ctypes.data if terms else None))
+    return out[:count]
 
 
 class Batch:

@@ -61,6 +61,10 @@ def test_bad_arguments_rejected_without_device(qvlib):
     r = qvlib.lib.qv_set_basis(None, 0)
     assert r == qvlib.QV_ERR_ARG and "NULL" in qvlib.qv_last_error()
     assert qvlib.lib.qv_destroy(None) == qvlib.QV_OK
+    # one-shot batch: no items, or a NULL state, is refused before any device work
+    assert qvlib.lib.qv_apply_batch(None, 1, None, 0, None, None) == qvlib.QV_ERR_ARG
+    items = (qvlib.qv_batch_item * 1)()
+    assert qvlib.lib.qv_apply_batch(items, 1, None, 0, None, None) == qvlib.QV_ERR_ARG
 
 
 def test_no_library_means_import_error(tmp_path, monkeypatch):

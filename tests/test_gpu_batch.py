@@ -30,6 +30,23 @@ def test_batch_ansatz_energies(qvlib, orc, cuda, flags):
         qv.qv_destroy(h)
 
 
+def test_apply_batch_one_shot(qvlib, orc, cuda):
+    """qv_apply_batch (create, one run, destroy in one call) gives the oracle's
+    <H> per state and leaves each state as the oracle's."""
+    qv = qvlib
+    n, layers, count = 11, 3, 5
+    terms = W.ansatz_hamiltonian(n)
+    circuits = [W.ansatz_circuit(n, layers, W.config_seed(2, 40 + c))[0] for c in range(count)]
+    states = [qv.qv_create(n, 0) for _ in range(count)]
+    got = qv.qv_apply_batch(list(zip(states, circuits)), terms)
+    want = np.array([orc.energy(n, g, terms) for g in circuits])
+    assert np.max(np.abs(got - want)) <= 2e-5
+    for h, g in zip(states, circuits):
+        assert np.linalg.norm(qv.qv_get_state(h).astype(complex) - orc.run(n, g)) <= 1e-5
+    for h in states:
+        qv.qv_destroy(h)
+
+
 @pytest.mark.parametrize("dtype", [0, 1])
 def test_batch_uneven_sizes(qvlib, orc, cuda, dtype):
     """Random circuits of uneven qubit counts and depths, several tile sizes."""
