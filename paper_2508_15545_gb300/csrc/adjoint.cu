@@ -68,6 +68,7 @@ __global__ void __launch_bounds__(kThreads) pauli_apply_kernel(const R *__restri
     __syncthreads();
     for (uint64_t j = uint64_t(blockIdx.x) * kThreads + threadIdx.x; j < N; j += uint64_t(gridDim.x) * kThreads) {
         R ar = 0, ai = 0;
+#pragma unroll 4  // lets the partner loads of several groups be in flight together
         for (int q = 0; q < ng; ++q) {
             const uint64_t src = j ^ g[q].x;
             R cr, ci;

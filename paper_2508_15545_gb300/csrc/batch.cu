@@ -164,6 +164,7 @@ __global__ void __launch_bounds__(kBThreads) batch_pauli_kernel(R *const *amps, 
     CompSum<R> acc;
     for (uint64_t i = i0 + threadIdx.x; i < i1; i += kBThreads) {
         const R ar = a[2 * i], ai = a[2 * i + 1];
+#pragma unroll 4  // lets the partner loads of several groups be in flight together
         for (int q = 0; q < ng; ++q) {
             const uint64_t j = i ^ g[q].x;
             const R br = a[2 * j], bi = a[2 * j + 1];

@@ -256,6 +256,7 @@ __global__ void __launch_bounds__(kThreads) pauli_all_kernel(const R *__restrict
     CompSum<R> acc;
     for (uint64_t i = uint64_t(blockIdx.x) * kThreads + threadIdx.x; i < N; i += uint64_t(gridDim.x) * kThreads) {
         const R ar = amp[2 * i], ai = amp[2 * i + 1];
+#pragma unroll 4  // lets the partner loads of several groups be in flight together
         for (int q = 0; q < ng; ++q) {
             const uint64_t j = i ^ g[q].x;
             const R br = amp[2 * j], bi = amp[2 * j + 1];
