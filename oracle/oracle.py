@@ -63,8 +63,6 @@ def load(path: str):
     L.orc_expect_pauli.restype = ctypes.c_double
     L.orc_apply_pauli_sum.argtypes = [c128p, c128p, ctypes.c_int, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
-    L.orc_inner.argtypes = [c128p, c128p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
-                            ctypes.POINTER(ctypes.c_double)]
     return L
 
 
@@ -217,12 +215,6 @@ def sample(psi: np.ndarray, u) -> np.ndarray:
     idx = np.searchsorted(cdf, np.asarray(u, dtype=np.float64) * total, side="right")
     last = int(np.nonzero(p)[0][-1])
     return np.minimum(idx, last).astype(np.uint64)
-
-
-def inner(a: np.ndarray, b: np.ndarray) -> complex:
-    re, im = ctypes.c_double(), ctypes.c_double()
-    lib().orc_inner(_ptr(a), _ptr(b), _check_state(a), ctypes.byref(re), ctypes.byref(im))
-    return complex(re.value, im.value)
 
 
 # ----------------------------------------------------------------------------

@@ -245,12 +245,3 @@ void orc_apply_pauli_sum(const cplx *psi, cplx *out, int n, const double *coeff,
     }
 }
 
-/* sum_i conj(a_i) b_i */
-void orc_inner(const cplx *a, const cplx *b, int n, double *re, double *im)
-{
-    const uint64_t dim = (uint64_t)1 << n;
-    cplx s = 0;
-    for (uint64_t i = 0; i < dim; ++i) s += conj(a[i]) * b[i];
-    *re = creal(s);
-    *im = cimag(s);
-}
