@@ -15,12 +15,10 @@
 //     counted per segment;
 //  4. one block: exclusive prefix of the counts; then each shot's place in the
 //     shot list ordered by segment (counting sort);
-//  5. per segment holding shots: FP64 sums of runs of its probabilities in shared
-//     memory, a prefix over the runs, and per shot a binary search over the runs
-//     and a short sequential search inside one.
+//  5. per segment holding shots: its amplitudes in shared memory, sums of runs of
+//     16 probabilities (FP64 per run), a prefix over the runs, and per shot a
+//     binary search over the runs and a short sequential search inside one.
 #include <algorithm>
-#include <cmath>
-#include <vector>
 
 #include "qv_device.cuh"
 #include "qv_internal.h"
