@@ -177,6 +177,21 @@ qv_status qv_apply_circuit(qv_state *s, const qv_gate *g, size_t ng, const qv_pl
  * operations. Host only. */
 qv_status qv_plan_info(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t out[4]);
 
+/* The CUDA source that the compiled fused engine generates for pass `pass`
+ * (0-based) of the plan qv_plan_info describes, for inspection: *len = its
+ * length; when cap > 0, up to cap - 1 bytes and a terminating NUL are written
+ * to buf. QV_ERR_ARG for a pass outside the plan or with QV_PLAN_INTERPRET
+ * (the interpreting engine compiles nothing). Host only. */
+qv_status qv_plan_source(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t pass,
+                         char *buf, size_t cap, size_t *len);
+
+/* Compiles every pass of that plan with NVRTC for sm_103a without a GPU or a
+ * driver, as the compiled engine would before launching them: out[0] = passes
+ * compiled, out[1] = generated source bytes. QV_ERR_UNSUPPORTED when NVRTC
+ * cannot be loaded, QV_ERR_CUDA (with the start of the compiler log in
+ * qv_last_error) when a pass does not compile. Host only. */
+qv_status qv_plan_compile(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int64_t out[2]);
+
 /* Algorithmic cost of the fused plan of g[0..ng) (host only, as qv_plan_info):
  * out[0] = HBM bytes, one read and one write of the state per pass;
  * out[1] = floating-point operations: per amplitude and on-chip operation,

@@ -182,23 +182,54 @@ qv_status to_pgates(const qv_gate *g, size_t ng, std::vector<plan::PGate> &out)
     return QV_OK;
 }
 
-qv_status plan_info(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t out[4],
-                    double cost[2])
+// The fused-mode plan of g as a device-memory state would get it (host only:
+// NVRTC is not consulted; the compiled complex64 engine's 4x4 pair ops unless
+// interpreting or QV_PLAN_NO_PAIRS).
+qv_status plan_host(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts,
+                    std::vector<plan::Pass> &passes, plan::PlanStats &st)
 {
     int K = (opts && opts->tile_bits) ? opts->tile_bits
                                       : tuned_tile_bits(n, dt, opts && (opts->flags & QV_PLAN_INTERPRET));
     if (K < plan::kMinK || K > plan::kMaxK || K > n) return fail(QV_ERR_ARG, "tile_bits %d unsupported for n = %d", K, n);
     std::vector<plan::PGate> pg;
     QV_TRY(to_pgates(g, ng, pg));
-    std::vector<plan::Pass> passes;
-    plan::PlanStats st;
     std::string err;
     const int flags = opts ? opts->flags : 0;
     const bool fuse = !(flags & QV_PLAN_NO_FUSION);
-    // as the compiled complex64 engine plans it (host only: NVRTC is not consulted)
     const bool pairs = dt == QV_C64 && !(flags & (QV_PLAN_INTERPRET | QV_PLAN_NO_PAIRS));
     if (!plan::make_plan(n, K, dt == QV_C64, fuse, pairs, pg, passes, st, err))
         return fail(QV_ERR_UNSUPPORTED, "planner: %s", err.c_str());
+    return QV_OK;
+}
+
+qv_status plan_source(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int pass,
+                      std::string &src)
+{
+    if (opts && (opts->flags & QV_PLAN_INTERPRET)) return fail(QV_ERR_ARG, "the interpreting engine compiles no passes");
+    std::vector<plan::Pass> passes;
+    plan::PlanStats st;
+    QV_TRY(plan_host(n, dt, g, ng, opts, passes, st));
+    if (pass < 0 || size_t(pass) >= passes.size())
+        return fail(QV_ERR_ARG, "pass %d outside [0, %zu)", pass, passes.size());
+    src = jit_pass_source(passes[size_t(pass)], dt == QV_C64);
+    return QV_OK;
+}
+
+qv_status plan_compile(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int64_t out[2])
+{
+    if (opts && (opts->flags & QV_PLAN_INTERPRET)) return fail(QV_ERR_ARG, "the interpreting engine compiles no passes");
+    std::vector<plan::Pass> passes;
+    plan::PlanStats st;
+    QV_TRY(plan_host(n, dt, g, ng, opts, passes, st));
+    return jit_compile_host(passes, dt == QV_C64, out);
+}
+
+qv_status plan_info(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t out[4],
+                    double cost[2])
+{
+    std::vector<plan::Pass> passes;
+    plan::PlanStats st;
+    QV_TRY(plan_host(n, dt, g, ng, opts, passes, st));
     if (out) {
         out[0] = st.passes;
         out[1] = st.stages;

@@ -13,6 +13,7 @@
 #include <nvrtc.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <cstdio>
 #include <map>
@@ -38,7 +39,8 @@ using plan::kRegBits;
 // Both are opened with dlopen so that libqv.so itself loads on machines
 // without a GPU driver (the host-only entry points still work there).
 struct JitApi {
-    bool ok = false;
+    bool ok = false;        // NVRTC and the driver: compile and launch
+    bool nvrtc_ok = false;  // NVRTC alone: compile on a host without a GPU driver
     std::string why;
     nvrtcResult (*create)(nvrtcProgram *, const char *, const char *, int, const char *const *, const char *const *);
     nvrtcResult (*compile)(nvrtcProgram, int, const char *const *);
@@ -64,8 +66,8 @@ const JitApi &api()
         void *h = dlopen("libnvrtc.so.13", RTLD_NOW | RTLD_LOCAL);
         if (!h) h = dlopen("libnvrtc.so", RTLD_NOW | RTLD_LOCAL);
         void *d = dlopen("libcuda.so.1", RTLD_NOW | RTLD_LOCAL);
-        if (!h || !d) {
-            n.why = !h ? "libnvrtc.so not found" : "libcuda.so.1 not found";
+        if (!h) {
+            n.why = "libnvrtc.so not found";
             return;
         }
         bool all = true;
@@ -80,6 +82,15 @@ const JitApi &api()
         sym(h, n.cubin_size, "nvrtcGetCUBINSize");
         sym(h, n.cubin, "nvrtcGetCUBIN");
         sym(h, n.destroy, "nvrtcDestroyProgram");
+        n.nvrtc_ok = all;
+        if (!all) {
+            n.why = "libnvrtc.so lacks a needed symbol";
+            return;
+        }
+        if (!d) {
+            n.why = "libcuda.so.1 not found";
+            return;
+        }
         sym(d, n.module_load, "cuModuleLoadData");
         sym(d, n.get_function, "cuModuleGetFunction");
         sym(d, n.set_attr, "cuFuncSetAttribute");
@@ -1003,6 +1014,38 @@ bool jit_available(std::string *why)
     const JitApi &N = api();
     if (!N.ok && why) *why = N.why;
     return N.ok;
+}
+
+std::string jit_pass_source(const plan::Pass &p, bool c64) { return gen_source(p, c64); }
+
+qv_status jit_compile_host(const std::vector<plan::Pass> &passes, bool c64, int64_t out[2])
+{
+    const JitApi &N = api();
+    if (!N.nvrtc_ok) return fail(QV_ERR_UNSUPPORTED, "NVRTC unavailable: %s", N.why.c_str());
+    const size_t np = passes.size();
+    std::vector<std::string> srcs(np), errs(np);
+    std::vector<char> ok(np, 0);
+    int64_t bytes = 0;
+    for (size_t i = 0; i < np; ++i) {
+        srcs[i] = gen_source(passes[i], c64);
+        bytes += int64_t(srcs[i].size());
+    }
+    const size_t nt = std::max<size_t>(1, std::min<size_t>(np, std::max(1u, std::thread::hardware_concurrency())));
+    std::atomic<size_t> next{0};
+    std::vector<std::thread> th;
+    for (size_t t = 0; t < nt; ++t)
+        th.emplace_back([&] {
+            for (size_t i; (i = next.fetch_add(1)) < np;) {
+                std::vector<char> cubin;
+                ok[i] = compile_one(srcs[i], cubin, errs[i]) ? 1 : 0;
+            }
+        });
+    for (auto &x : th) x.join();
+    for (size_t i = 0; i < np; ++i)
+        if (!ok[i]) return fail(QV_ERR_CUDA, "pass %zu: %s", i, errs[i].c_str());
+    out[0] = int64_t(np);
+    out[1] = bytes;
+    return QV_OK;
 }
 
 namespace {

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <unistd.h>
 #include <mutex>
@@ -387,6 +388,36 @@ qv_status qv_plan_cost(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv
     if (ng && !g) return fail(QV_ERR_ARG, "gate list is NULL");
     for (size_t k = 0; k < ng; ++k) QV_TRY(validate_gate(g[k], n, k));
     return plan_info(n, dt, g, ng, opts, nullptr, out);
+}
+
+qv_status qv_plan_source(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t pass,
+                         char *buf, size_t cap, size_t *len)
+{
+    if (!len) return fail(QV_ERR_ARG, "len is NULL");
+    if (cap && !buf) return fail(QV_ERR_ARG, "buf is NULL");
+    if (n < 1 || n > 40) return fail(QV_ERR_ARG, "n = %d outside [1, 40]", n);
+    if (dt != QV_C64 && dt != QV_C128) return fail(QV_ERR_ARG, "bad dtype %d", int(dt));
+    if (ng && !g) return fail(QV_ERR_ARG, "gate list is NULL");
+    for (size_t k = 0; k < ng; ++k) QV_TRY(validate_gate(g[k], n, k));
+    std::string src;
+    QV_TRY(plan_source(n, dt, g, ng, opts, pass, src));
+    *len = src.size();
+    if (cap) {
+        const size_t m = std::min(cap - 1, src.size());
+        std::memcpy(buf, src.data(), m);
+        buf[m] = '\0';
+    }
+    return QV_OK;
+}
+
+qv_status qv_plan_compile(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int64_t out[2])
+{
+    if (!out) return fail(QV_ERR_ARG, "out is NULL");
+    if (n < 1 || n > 40) return fail(QV_ERR_ARG, "n = %d outside [1, 40]", n);
+    if (dt != QV_C64 && dt != QV_C128) return fail(QV_ERR_ARG, "bad dtype %d", int(dt));
+    if (ng && !g) return fail(QV_ERR_ARG, "gate list is NULL");
+    for (size_t k = 0; k < ng; ++k) QV_TRY(validate_gate(g[k], n, k));
+    return plan_compile(n, dt, g, ng, opts, out);
 }
 
 qv_status qv_permute_qubits(qv_state *s, const int32_t *perm)

@@ -93,6 +93,11 @@ def _load():
                          ctypes.POINTER(qv_plan_opts), ctypes.POINTER(ctypes.c_int32)],
         "qv_plan_cost": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(qv_gate), ctypes.c_size_t,
                          ctypes.POINTER(qv_plan_opts), ctypes.POINTER(ctypes.c_double)],
+        "qv_plan_source": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(qv_gate), ctypes.c_size_t,
+                           ctypes.POINTER(qv_plan_opts), ctypes.c_int32, ctypes.c_char_p, ctypes.c_size_t,
+                           ctypes.POINTER(ctypes.c_size_t)],
+        "qv_plan_compile": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(qv_gate), ctypes.c_size_t,
+                            ctypes.POINTER(qv_plan_opts), ctypes.POINTER(ctypes.c_int64)],
         "qv_norm2": [_H, ctypes.POINTER(ctypes.c_double)],
         "qv_expect_z": [_H, P, P, ctypes.POINTER(ctypes.c_double)],
         "qv_expect_pauli": [_H, ctypes.POINTER(qv_pauli_term), ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)],
@@ -291,6 +296,33 @@ def qv_plan_cost(n: int, dtype: int, gates, tile_bits: int = 0, flags: int = 0) 
     opts = plan_opts(QV_MODE_FUSED, tile_bits, flags)
     _check(lib.qv_plan_cost(n, dtype, arr, ng, ctypes.byref(opts), out))
     return {"bytes": out[0], "flops": out[1]}
+
+
+def qv_plan_source(n: int, dtype: int, gates, pass_index: int, tile_bits: int = 0, flags: int = 0) -> str:
+    """CUDA source of compiled fused pass ``pass_index`` (host only)."""
+    if isinstance(gates, tuple) and len(gates) == 2 and isinstance(gates[1], int):
+        arr, ng = gates
+    else:
+        arr, ng = gates_to_c(gates), len(gates)
+    opts = plan_opts(QV_MODE_FUSED, tile_bits, flags)
+    ln = ctypes.c_size_t()
+    _check(lib.qv_plan_source(n, dtype, arr, ng, ctypes.byref(opts), pass_index, None, 0, ctypes.byref(ln)))
+    buf = ctypes.create_string_buffer(ln.value + 1)
+    _check(lib.qv_plan_source(n, dtype, arr, ng, ctypes.byref(opts), pass_index, buf, ln.value + 1,
+                              ctypes.byref(ln)))
+    return buf.value.decode()
+
+
+def qv_plan_compile(n: int, dtype: int, gates, tile_bits: int = 0, flags: int = 0) -> dict:
+    """Compiles every pass of the fused plan with NVRTC (host only, no GPU)."""
+    if isinstance(gates, tuple) and len(gates) == 2 and isinstance(gates[1], int):
+        arr, ng = gates
+    else:
+        arr, ng = gates_to_c(gates), len(gates)
+    opts = plan_opts(QV_MODE_FUSED, tile_bits, flags)
+    out = (ctypes.c_int64 * 2)()
+    _check(lib.qv_plan_compile(n, dtype, arr, ng, ctypes.byref(opts), out))
+    return {"passes": int(out[0]), "source_bytes": int(out[1])}
 
 
 def qv_permute_qubits(h: int, perm: Sequence[int]):

@@ -91,3 +91,59 @@ def test_swap_of_two_outside_qubits_first(qv, flags):
     info = qv.qv_plan_info(n, 0, gates, tile_bits=10, flags=flags)
     assert info["passes"] >= 1
 
+
+
+def _compile_or_skip(qv, *args, **kw):
+    try:
+        return qv.qv_plan_compile(*args, **kw)
+    except qv.QvError as e:
+        if e.status == qv.QV_ERR_UNSUPPORTED:
+            pytest.skip(f"NVRTC unavailable: {e}")
+        raise
+
+
+# (dtype, tile bits, flags): compiled engine with fusion and pair ops, no
+# fusion, fusion without pair ops; complex128
+@pytest.mark.parametrize("dtype,k,flags", [(0, 10, 0), (0, 11, 0), (0, 12, 0), (0, 11, 1), (0, 12, 4),
+                                           (1, 10, 0), (1, 12, 0)])
+def test_generated_passes_compile_on_host(qv, dtype, k, flags):
+    """Every pass kernel the compiled engine would generate for a circuit of
+    every gate kind (controls inside and outside the tile, SWAPs) compiles with
+    NVRTC for sm_103a, without a GPU."""
+    from paper_2508_15545_gb300 import workloads as W
+    n = 13
+    gates = W.random_gate_list(n, 160, seed=700 + 10 * k + dtype, ctrl_prob=0.4)
+    info = qv.qv_plan_info(n, dtype, gates, tile_bits=k, flags=flags)
+    got = _compile_or_skip(qv, n, dtype, gates, tile_bits=k, flags=flags)
+    assert got["passes"] == info["passes"] and got["source_bytes"] > 0
+
+
+def test_bench_like_circuit_compiles_on_host(qv):
+    """The passes of a 20-qubit random circuit of the bench's recipe (U3 layers
+    and brickwork CNOTs), at the default tile size."""
+    gates = random_circuit(20, 10, config_seed(1))
+    got = _compile_or_skip(qv, 20, 0, gates)
+    assert got["passes"] == qv.qv_plan_info(20, 0, gates)["passes"]
+
+
+def test_single_stage_relabel_pass_orders_stores_after_loads(qv):
+    """A pass with one stage whose SWAP relabels change the store layout needs
+    a block barrier between its loads and its stores (other warps may not have
+    loaded the positions a warp stores to); one whose layout is unchanged
+    stores exactly what each thread loaded and needs none."""
+    swap = qv.qv_plan_source(10, 0, [Gate("swap", 6, target2=8)], 0, tile_bits=10)
+    assert swap.count("__syncthreads") == 1
+    u3 = qv.qv_plan_source(10, 0, [Gate("u3", 6, theta=(0.3, 0.2, 0.1))], 0, tile_bits=10)
+    assert u3.count("__syncthreads") == 0
+    c128 = qv.qv_plan_source(10, 1, [Gate("swap", 7, target2=9)], 0, tile_bits=10)
+    assert c128.count("__syncthreads") == 1
+
+
+def test_plan_source_rejects_bad_args(qv):
+    g = [Gate("h", 3)]
+    with pytest.raises(qv.QvError) as e:
+        qv.qv_plan_source(12, 0, g, 5)
+    assert e.value.status == qv.QV_ERR_ARG
+    with pytest.raises(qv.QvError) as e:
+        qv.qv_plan_source(12, 0, g, 0, flags=qv.QV_PLAN_INTERPRET)
+    assert e.value.status == qv.QV_ERR_ARG
