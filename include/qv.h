@@ -187,10 +187,12 @@ qv_status qv_plan_source(int n, qv_dtype dt, const qv_gate *g, size_t ng, const 
 
 /* Compiles every pass of that plan with NVRTC for sm_103a without a GPU or a
  * driver, as the compiled engine would before launching them: out[0] = passes
- * compiled, out[1] = generated source bytes. QV_ERR_UNSUPPORTED when NVRTC
- * cannot be loaded, QV_ERR_CUDA (with the start of the compiler log in
- * qv_last_error) when a pass does not compile. Host only. */
-qv_status qv_plan_compile(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int64_t out[2]);
+ * compiled, out[1] = generated source bytes, out[2] = the most registers a
+ * thread of any pass uses (ptxas report), out[3] = passes whose registers
+ * spill to local memory. QV_ERR_UNSUPPORTED when NVRTC cannot be loaded,
+ * QV_ERR_CUDA (with the start of the compiler log in qv_last_error) when a
+ * pass does not compile. Host only. */
+qv_status qv_plan_compile(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int64_t out[4]);
 
 /* Algorithmic cost of the fused plan of g[0..ng) (host only, as qv_plan_info):
  * out[0] = HBM bytes, one read and one write of the state per pass;

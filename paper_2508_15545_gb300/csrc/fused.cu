@@ -215,7 +215,7 @@ qv_status plan_source(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_
     return QV_OK;
 }
 
-qv_status plan_compile(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int64_t out[2])
+qv_status plan_compile(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int64_t out[4])
 {
     if (opts && (opts->flags & QV_PLAN_INTERPRET)) return fail(QV_ERR_ARG, "the interpreting engine compiles no passes");
     std::vector<plan::Pass> passes;

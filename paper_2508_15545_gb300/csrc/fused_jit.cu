@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
 #include <cstring>
 #include <cstdio>
 #include <map>
@@ -973,7 +974,8 @@ namespace {
 std::mutex g_cache_mu;
 std::map<std::pair<int, std::string>, std::shared_ptr<Compiled>> g_cache;
 
-bool compile_one(const std::string &src, std::vector<char> &cubin, std::string &err)
+// With `log`, ptxas also reports registers and spills (-v) into *log.
+bool compile_one(const std::string &src, std::vector<char> &cubin, std::string &err, std::string *log = nullptr)
 {
     const JitApi &N = api();
     nvrtcProgram prog;
@@ -981,8 +983,14 @@ bool compile_one(const std::string &src, std::vector<char> &cubin, std::string &
         err = "nvrtcCreateProgram failed";
         return false;
     }
-    const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "--fmad=true"};
-    const nvrtcResult rc = N.compile(prog, 3, opts);
+    const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "--fmad=true", "--ptxas-options=-v"};
+    const nvrtcResult rc = N.compile(prog, log ? 4 : 3, opts);
+    if (log && rc == NVRTC_SUCCESS) {
+        size_t ls = 0;
+        N.log_size(prog, &ls);
+        log->assign(ls, '\0');
+        if (ls) N.log(prog, &(*log)[0]);
+    }
     if (rc != NVRTC_SUCCESS) {
         size_t ls = 0;
         N.log_size(prog, &ls);
@@ -1018,12 +1026,27 @@ bool jit_available(std::string *why)
 
 std::string jit_pass_source(const plan::Pass &p, bool c64) { return gen_source(p, c64); }
 
-qv_status jit_compile_host(const std::vector<plan::Pass> &passes, bool c64, int64_t out[2])
+namespace {
+// The number before `key` in a ptxas -v report ("Used 128 registers",
+// "44 bytes spill stores"); -1 when absent.
+long ptxas_number(const std::string &log, const char *key)
+{
+    const size_t p = log.find(key);
+    if (p == std::string::npos) return -1;
+    size_t e = p;
+    while (e > 0 && log[e - 1] == ' ') --e;
+    size_t b = e;
+    while (b > 0 && log[b - 1] >= '0' && log[b - 1] <= '9') --b;
+    return b < e ? std::atol(log.c_str() + b) : -1;
+}
+}  // namespace
+
+qv_status jit_compile_host(const std::vector<plan::Pass> &passes, bool c64, int64_t out[4])
 {
     const JitApi &N = api();
     if (!N.nvrtc_ok) return fail(QV_ERR_UNSUPPORTED, "NVRTC unavailable: %s", N.why.c_str());
     const size_t np = passes.size();
-    std::vector<std::string> srcs(np), errs(np);
+    std::vector<std::string> srcs(np), errs(np), logs(np);
     std::vector<char> ok(np, 0);
     int64_t bytes = 0;
     for (size_t i = 0; i < np; ++i) {
@@ -1037,14 +1060,20 @@ qv_status jit_compile_host(const std::vector<plan::Pass> &passes, bool c64, int6
         th.emplace_back([&] {
             for (size_t i; (i = next.fetch_add(1)) < np;) {
                 std::vector<char> cubin;
-                ok[i] = compile_one(srcs[i], cubin, errs[i]) ? 1 : 0;
+                ok[i] = compile_one(srcs[i], cubin, errs[i], &logs[i]) ? 1 : 0;
             }
         });
     for (auto &x : th) x.join();
-    for (size_t i = 0; i < np; ++i)
+    int64_t regs = 0, spilling = 0;
+    for (size_t i = 0; i < np; ++i) {
         if (!ok[i]) return fail(QV_ERR_CUDA, "pass %zu: %s", i, errs[i].c_str());
+        regs = std::max<int64_t>(regs, ptxas_number(logs[i], "registers"));
+        spilling += ptxas_number(logs[i], "bytes spill stores") > 0 ? 1 : 0;
+    }
     out[0] = int64_t(np);
     out[1] = bytes;
+    out[2] = regs;
+    out[3] = spilling;
     return QV_OK;
 }
 

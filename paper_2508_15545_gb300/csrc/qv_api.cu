@@ -410,7 +410,7 @@ qv_status qv_plan_source(int n, qv_dtype dt, const qv_gate *g, size_t ng, const 
     return QV_OK;
 }
 
-qv_status qv_plan_compile(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int64_t out[2])
+qv_status qv_plan_compile(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int64_t out[4])
 {
     if (!out) return fail(QV_ERR_ARG, "out is NULL");
     if (n < 1 || n > 40) return fail(QV_ERR_ARG, "n = %d outside [1, 40]", n);

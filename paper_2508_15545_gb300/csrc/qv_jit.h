@@ -15,9 +15,11 @@ bool jit_available(std::string *why);
 
 // Host only (no driver needed): the CUDA source of one compiled pass, and
 // NVRTC compilation of every pass of a plan (out[0] = passes, out[1] = source
-// bytes; QV_ERR_UNSUPPORTED without NVRTC, QV_ERR_CUDA with the log if one fails).
+// bytes, out[2] = most registers a thread of any pass uses, out[3] = passes
+// whose registers spill; QV_ERR_UNSUPPORTED without NVRTC, QV_ERR_CUDA with
+// the log if one fails).
 std::string jit_pass_source(const plan::Pass &p, bool c64);
-qv_status jit_compile_host(const std::vector<plan::Pass> &passes, bool c64, int64_t out[2]);
+qv_status jit_compile_host(const std::vector<plan::Pass> &passes, bool c64, int64_t out[4]);
 
 // Compiled kernels and packed coefficients of a plan, ready to launch again.
 struct JitProgram;

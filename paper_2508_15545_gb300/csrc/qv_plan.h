@@ -19,10 +19,10 @@ qv_status apply_fused(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_op
 qv_status plan_info(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t out[4],
                     double cost[2]);
 // Host only: the generated CUDA source of compiled pass `pass` of that plan,
-// and NVRTC compilation of all its passes (out[0] = passes, out[1] = source bytes).
+// and NVRTC compilation of all its passes (out as jit_compile_host).
 qv_status plan_source(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int pass,
                       std::string &src);
-qv_status plan_compile(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int64_t out[2]);
+qv_status plan_compile(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int64_t out[4]);
 
 // Bit q of every index moves to bit perm[q].
 qv_status apply_permutation(qv_state *s, const int32_t *perm);

@@ -320,9 +320,10 @@ def qv_plan_compile(n: int, dtype: int, gates, tile_bits: int = 0, flags: int = 
     else:
         arr, ng = gates_to_c(gates), len(gates)
     opts = plan_opts(QV_MODE_FUSED, tile_bits, flags)
-    out = (ctypes.c_int64 * 2)()
+    out = (ctypes.c_int64 * 4)()
     _check(lib.qv_plan_compile(n, dtype, arr, ng, ctypes.byref(opts), out))
-    return {"passes": int(out[0]), "source_bytes": int(out[1])}
+    return {"passes": int(out[0]), "source_bytes": int(out[1]), "max_registers": int(out[2]),
+            "spilling_passes": int(out[3])}
 
 
 def qv_permute_qubits(h: int, perm: Sequence[int]):

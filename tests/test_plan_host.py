@@ -124,6 +124,9 @@ def test_bench_like_circuit_compiles_on_host(qv):
     gates = random_circuit(20, 10, config_seed(1))
     got = _compile_or_skip(qv, 20, 0, gates)
     assert got["passes"] == qv.qv_plan_info(20, 0, gates)["passes"]
+    # the complex64 pass is built for 128 registers a thread (the next tile
+    # held in registers, 4 CTAs per SM at 2^11-amplitude tiles)
+    assert 0 < got["max_registers"] <= 128
 
 
 def test_single_stage_relabel_pass_orders_stores_after_loads(qv):
