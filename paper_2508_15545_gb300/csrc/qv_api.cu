@@ -370,23 +370,29 @@ qv_status qv_apply_circuit(qv_state *s, const qv_gate *g, size_t ng, const qv_pl
     return apply_fused(s, g, ng, opts);
 }
 
-qv_status qv_plan_info(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t out[4])
+namespace {
+// Arguments of the host-only planning calls: size, dtype and every gate.
+qv_status check_plan_args(int n, qv_dtype dt, const qv_gate *g, size_t ng)
 {
-    if (!out) return fail(QV_ERR_ARG, "out is NULL");
     if (n < 1 || n > 40) return fail(QV_ERR_ARG, "n = %d outside [1, 40]", n);
     if (dt != QV_C64 && dt != QV_C128) return fail(QV_ERR_ARG, "bad dtype %d", int(dt));
     if (ng && !g) return fail(QV_ERR_ARG, "gate list is NULL");
     for (size_t k = 0; k < ng; ++k) QV_TRY(validate_gate(g[k], n, k));
+    return QV_OK;
+}
+}  // namespace
+
+qv_status qv_plan_info(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t out[4])
+{
+    if (!out) return fail(QV_ERR_ARG, "out is NULL");
+    QV_TRY(check_plan_args(n, dt, g, ng));
     return plan_info(n, dt, g, ng, opts, out, nullptr);
 }
 
 qv_status qv_plan_cost(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, double out[2])
 {
     if (!out) return fail(QV_ERR_ARG, "out is NULL");
-    if (n < 1 || n > 40) return fail(QV_ERR_ARG, "n = %d outside [1, 40]", n);
-    if (dt != QV_C64 && dt != QV_C128) return fail(QV_ERR_ARG, "bad dtype %d", int(dt));
-    if (ng && !g) return fail(QV_ERR_ARG, "gate list is NULL");
-    for (size_t k = 0; k < ng; ++k) QV_TRY(validate_gate(g[k], n, k));
+    QV_TRY(check_plan_args(n, dt, g, ng));
     return plan_info(n, dt, g, ng, opts, nullptr, out);
 }
 
@@ -395,10 +401,7 @@ qv_status qv_plan_source(int n, qv_dtype dt, const qv_gate *g, size_t ng, const 
 {
     if (!len) return fail(QV_ERR_ARG, "len is NULL");
     if (cap && !buf) return fail(QV_ERR_ARG, "buf is NULL");
-    if (n < 1 || n > 40) return fail(QV_ERR_ARG, "n = %d outside [1, 40]", n);
-    if (dt != QV_C64 && dt != QV_C128) return fail(QV_ERR_ARG, "bad dtype %d", int(dt));
-    if (ng && !g) return fail(QV_ERR_ARG, "gate list is NULL");
-    for (size_t k = 0; k < ng; ++k) QV_TRY(validate_gate(g[k], n, k));
+    QV_TRY(check_plan_args(n, dt, g, ng));
     std::string src;
     QV_TRY(plan_source(n, dt, g, ng, opts, pass, src));
     *len = src.size();
@@ -413,10 +416,7 @@ qv_status qv_plan_source(int n, qv_dtype dt, const qv_gate *g, size_t ng, const 
 qv_status qv_plan_compile(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int64_t out[4])
 {
     if (!out) return fail(QV_ERR_ARG, "out is NULL");
-    if (n < 1 || n > 40) return fail(QV_ERR_ARG, "n = %d outside [1, 40]", n);
-    if (dt != QV_C64 && dt != QV_C128) return fail(QV_ERR_ARG, "bad dtype %d", int(dt));
-    if (ng && !g) return fail(QV_ERR_ARG, "gate list is NULL");
-    for (size_t k = 0; k < ng; ++k) QV_TRY(validate_gate(g[k], n, k));
+    QV_TRY(check_plan_args(n, dt, g, ng));
     return plan_compile(n, dt, g, ng, opts, out);
 }
 
