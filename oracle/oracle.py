@@ -31,13 +31,17 @@ class OrcGate(ctypes.Structure):
                 ("theta", ctypes.c_double * 3), ("m", ctypes.c_double * 8)]
 
 
-def build_oracle(force: bool = False) -> str:
-    """Compile qv_oracle.c into liboracle.so with gcc (plain -O2, no -ffast-math)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+def build_oracle(force: bool = False, openmp: bool = True, out: str | None = None) -> str:
+    """Compile qv_oracle.c with gcc (plain -O2, no -ffast-math) into
+    liboracle.so, or into ``out``. ``openmp`` splits the pair loops over
+    threads (same arithmetic per pair; the serial build gives the same bits)."""
+    lib = out or _LIB
+    if force or out or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+        tmp = lib + ".%d.tmp" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared"] + (["-fopenmp"] if openmp else [])
+        subprocess.check_call(cmd + ["-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, lib)
+    return lib
 
 
 _lib = None
@@ -63,6 +67,8 @@ def load(path: str):
     L.orc_expect_pauli.restype = ctypes.c_double
     L.orc_apply_pauli_sum.argtypes = [c128p, c128p, ctypes.c_int, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
+    L.orc_set_threads.argtypes = [ctypes.c_int]
+    L.orc_set_threads.restype = ctypes.c_int
     return L
 
 
@@ -71,6 +77,12 @@ def lib():
     if _lib is None:
         _lib = load(build_oracle())
     return _lib
+
+
+def set_threads(nthreads: int = 0) -> int:
+    """Threads of the oracle's parallel loops (0: keep the current number);
+    returns the number in effect (1 for a serial build)."""
+    return int(lib().orc_set_threads(int(nthreads)))
 
 
 def _ptr(a: np.ndarray) -> int:

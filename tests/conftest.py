@@ -11,6 +11,20 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+    config.addinivalue_line("markers", "oracle_fullsize: compares a full-size GPU result with the oracle "
+                            "(the oracle runs on a background thread from the end of collection)")
+
+
+def pytest_collection_finish(session):
+    """Start the full-size oracle states early when a test that needs them is
+    selected and a GPU is present, so the host cores work while the GPU
+    tests run."""
+    if not any(item.get_closest_marker("oracle_fullsize") for item in session.items):
+        return
+    import torch
+    if torch.cuda.is_available():
+        from tests import fullsize_oracle
+        fullsize_oracle.start()
 
 
 @pytest.fixture(scope="session")
@@ -35,3 +49,9 @@ def cuda():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     return torch
+
+
+@pytest.fixture(scope="session")
+def fullsize_oracle():
+    from tests import fullsize_oracle as F
+    return F.get()

@@ -159,7 +159,7 @@ def test_adjoint_tiled_sweep_mixed(qvlib, orc, cuda, dtype, n):
     psi0 = W.random_state(n, 9 + n)
     g1, e1, _, _ = _adjoint(qv, n, dtype, gates, terms, npar, psi0, sweep=1)
     ref = orc.param_shift_grad(n, gates, terms, npar, psi0)
-    tol = 2e-4 if dtype == 0 else 1e-10
+    tol = 1e-4 if dtype == 0 else 1e-10
     for sweep in (2, 3):
         g2, e2, before, after = _adjoint(qv, n, dtype, gates, terms, npar, psi0, sweep=sweep)
         assert e2 == pytest.approx(orc.energy(n, gates, terms, psi0), abs=tol)
