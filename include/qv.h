@@ -89,6 +89,10 @@ typedef enum {
 #define QV_PLAN_NO_PAIRS 4   /* fused mode: no 4x4 operations on two register qubits (the
                                 compiled complex64 kernel merges runs of operations on two
                                 qubits into one 4x4 when that takes fewer FP32 operations) */
+#define QV_PLAN_TENSOR 8     /* fused mode, complex64, tiles of 2^11 or 2^12: every stage of a
+                                pass multiplies its gates into one 16x16 complex matrix and
+                                applies it on the tensor cores (tcgen05, TF32 operands split
+                                in three products for FP32 accuracy) */
 
 typedef struct {
     int32_t mode;        /* qv_mode */
@@ -193,6 +197,35 @@ qv_status qv_plan_source(int n, qv_dtype dt, const qv_gate *g, size_t ng, const 
  * QV_ERR_CUDA (with the start of the compiler log in qv_last_error) when a
  * pass does not compile. Host only. */
 qv_status qv_plan_compile(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int64_t out[4]);
+
+/* One stage of a tensor-core plan (QV_PLAN_TENSOR), for inspection. A pass
+ * loads every tile of 2^k amplitudes; tile position p is physical qubit
+ * tile_qubit[p]. In a stage, thread t of a tile holds the 16 amplitudes whose
+ * tile positions are deposit(t; in_thr) | deposit(r; in_reg), r = 0..15 (bit j
+ * of r at position in_reg[j], bit b of t at in_thr[b]); the stage replaces that
+ * vector by M r-vector (M row-major 16x16, variant 1 where the physical qubit
+ * ext is 1 in the tile's index, else variant 0) and writes it back through the
+ * positions of out_reg / out_thr (which differ from the input positions only
+ * after SWAP gates, exchanges of position labels). A stage without a matrix
+ * only changes the layout. */
+typedef struct {
+    int32_t k;             /* tile bits */
+    int32_t nstages;       /* stages of this pass */
+    int32_t tile_qubit[12];
+    int32_t in_reg[4];
+    int32_t in_thr[8];     /* k - 4 entries used */
+    int32_t out_reg[4];
+    int32_t out_thr[8];
+    int32_t has_matrix;
+    int32_t ext;           /* -1: one matrix for every tile */
+    qv_c128 m[2][256];
+} qv_tc_stage;
+
+/* Stage `stage` of pass `pass` of the tensor-core plan of g[0..ng) (opts must
+ * carry QV_PLAN_TENSOR; complex64). QV_ERR_ARG for a pass or stage outside the
+ * plan. Host only: the planner's output, not an execution of it. */
+qv_status qv_plan_tc_stage(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t pass,
+                           int32_t stage, qv_tc_stage *out);
 
 /* Algorithmic cost of the fused plan of g[0..ng) (host only, as qv_plan_info):
  * out[0] = HBM bytes, one read and one write of the state per pass;

@@ -197,8 +197,49 @@ qv_status plan_host(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_pl
     const int flags = opts ? opts->flags : 0;
     const bool fuse = !(flags & QV_PLAN_NO_FUSION);
     const bool pairs = dt == QV_C64 && !(flags & (QV_PLAN_INTERPRET | QV_PLAN_NO_PAIRS));
-    if (!plan::make_plan(n, K, dt == QV_C64, fuse, pairs, pg, passes, st, err))
+    const bool tc = (flags & QV_PLAN_TENSOR) != 0;
+    if (tc && (dt != QV_C64 || (flags & QV_PLAN_INTERPRET)))
+        return fail(QV_ERR_ARG, "tensor-core passes are compiled and complex64 only");
+    if (!plan::make_plan(n, K, dt == QV_C64, fuse, pairs, pg, passes, st, err, tc))
         return fail(QV_ERR_UNSUPPORTED, "planner: %s", err.c_str());
+    return QV_OK;
+}
+
+qv_status plan_tc_stage(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int pass,
+                        int stage, qv_tc_stage *out)
+{
+    if (!opts || !(opts->flags & QV_PLAN_TENSOR)) return fail(QV_ERR_ARG, "not a tensor-core plan (QV_PLAN_TENSOR)");
+    std::vector<plan::Pass> passes;
+    plan::PlanStats st;
+    QV_TRY(plan_host(n, dt, g, ng, opts, passes, st));
+    if (pass < 0 || size_t(pass) >= passes.size()) return fail(QV_ERR_ARG, "pass %d outside [0, %zu)", pass, passes.size());
+    const plan::Pass &P = passes[size_t(pass)];
+    if (stage < 0 || size_t(stage) >= P.stages.size())
+        return fail(QV_ERR_ARG, "stage %d outside [0, %zu)", stage, P.stages.size());
+    const plan::Stage &S = P.stages[size_t(stage)];
+    std::memset(out, 0, sizeof(*out));
+    out->k = P.k;
+    out->nstages = int32_t(P.stages.size());
+    for (int p = 0; p < 12; ++p) out->tile_qubit[p] = -1;
+    for (int p = 0; p < plan::kChunkBits; ++p) out->tile_qubit[p] = p;
+    for (int j = 0; j < P.k - plan::kChunkBits; ++j) out->tile_qubit[plan::kChunkBits + j] = P.s_high[j];
+    for (int j = 0; j < plan::kRegBits; ++j) {
+        out->in_reg[j] = S.in.P[j];
+        out->out_reg[j] = S.out.P[j];
+    }
+    for (int b = 0; b < 8; ++b) {
+        out->in_thr[b] = b < P.k - plan::kRegBits ? S.in.Q[b] : -1;
+        out->out_thr[b] = b < P.k - plan::kRegBits ? S.out.Q[b] : -1;
+    }
+    out->has_matrix = S.mat >= 0;
+    out->ext = S.ext;
+    if (S.mat >= 0)
+        for (int v = 0; v < (S.ext >= 0 ? 2 : 1); ++v)
+            for (int e = 0; e < plan::kTcSlot; ++e) {
+                const cd z = P.tcm[size_t(S.mat + v) * plan::kTcSlot + e];
+                out->m[v][e].re = z.real();
+                out->m[v][e].im = z.imag();
+            }
     return QV_OK;
 }
 
@@ -234,7 +275,7 @@ qv_status plan_info(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_pl
         out[0] = st.passes;
         out[1] = st.stages;
         out[2] = st.transposes;
-        out[3] = st.ops;
+        out[3] = (opts && (opts->flags & QV_PLAN_TENSOR)) ? st.tc_mats : st.ops;
     }
     if (cost) {
         const double N = std::ldexp(1.0, n);
@@ -253,6 +294,14 @@ qv_status apply_fused(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_op
     const int flags = opts ? opts->flags : 0;
     const bool fuse = !(flags & QV_PLAN_NO_FUSION);
     const bool jit = !(flags & QV_PLAN_INTERPRET) && jit_available(nullptr);
+    const bool tc = (flags & QV_PLAN_TENSOR) != 0;
+    if (tc) {
+        if (s->dt != QV_C64 || (flags & QV_PLAN_INTERPRET))
+            return fail(QV_ERR_ARG, "tensor-core passes are compiled and complex64 only");
+        if (K < 11) return fail(QV_ERR_ARG, "tensor-core passes need tiles of 2^11 or 2^12 amplitudes");
+        std::string why;
+        if (!jit_available(&why)) return fail(QV_ERR_UNSUPPORTED, "tensor-core passes need NVRTC: %s", why.c_str());
+    }
     if (!s->plan) s->plan = new PlanCache;
     PlanCache &C = *s->plan;
     const bool hit = C.K == K && C.flags == flags && C.key.size() == ng &&
@@ -265,7 +314,7 @@ qv_status apply_fused(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_op
         std::string err;
         // 4x4 operations exist only in the compiled complex64 kernel
         const bool pairs = jit && s->dt == QV_C64 && !(flags & QV_PLAN_NO_PAIRS);
-        if (!plan::make_plan(s->n, K, s->dt == QV_C64, fuse, pairs, pg, passes, st, err))
+        if (!plan::make_plan(s->n, K, s->dt == QV_C64, fuse, pairs, pg, passes, st, err, tc))
             return fail(QV_ERR_UNSUPPORTED, "planner: %s", err.c_str());
         C.key.clear();  // invalid until the new plan is complete
         C.passes = std::move(passes);

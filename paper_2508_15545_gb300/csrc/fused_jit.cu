@@ -53,6 +53,7 @@ struct JitApi {
     CUresult (*module_load)(CUmodule *, const void *);
     CUresult (*get_function)(CUfunction *, CUmodule, const char *);
     CUresult (*set_attr)(CUfunction, CUfunction_attribute, int);
+    CUresult (*get_attr)(int *, CUfunction_attribute, CUfunction);
     CUresult (*occupancy)(int *, CUfunction, int, size_t);
     CUresult (*launch)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, CUstream,
                        void **, void **);
@@ -95,6 +96,7 @@ const JitApi &api()
         sym(d, n.module_load, "cuModuleLoadData");
         sym(d, n.get_function, "cuModuleGetFunction");
         sym(d, n.set_attr, "cuFuncSetAttribute");
+        sym(d, n.get_attr, "cuFuncGetAttribute");
         sym(d, n.occupancy, "cuOccupancyMaxActiveBlocksPerMultiprocessor");
         sym(d, n.launch, "cuLaunchKernel");
         sym(d, n.err_string, "cuGetErrorString");
@@ -629,6 +631,314 @@ void emit_tile_body(std::ostream &o, const plan::Pass &p, bool c64, bool l2_load
     }
 }
 
+// ---------------------------------------------------------------- tensor-core passes (complex64)
+// A pass of a tensor-core plan: every stage multiplies the 16 amplitudes a
+// thread holds (its four register positions) by the stage's 16x16 complex
+// matrix on the tensor cores. Thread t of the tile is row t of an M = 128
+// product (two products for 2^12 tiles): the row's 32 real components (16 re,
+// 16 im) are the A operand, written to tensor memory with tcgen05.st; the
+// matrix in real form [[Re, -Im], [Im, Re]] (32 x 32, K-major) is the B operand
+// in shared memory; the 32 outputs land in tensor memory and return to the
+// thread with tcgen05.ld. TF32 keeps 11 significant bits, so each operand is
+// split into a TF32 head and a TF32 tail (x = hi + lo) and the product is
+// hi*hi + lo*hi + hi*lo, accumulated in FP32 (the lo*lo term is below FP32
+// rounding). Between stages the tile moves through shared memory (one 8-byte
+// word per amplitude, swizzled) into the next stage's layout.
+
+const char *kPreludeTc = R"PRELUDE(
+typedef unsigned long long u64;
+typedef unsigned int u32;
+#define QI __device__ __forceinline__
+QI u32 smem_u32(const void *p) { return (u32)__cvta_generic_to_shared(p); }
+QI float tf32r(float x) { u32 r; asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x)); return __uint_as_float(r); }
+// K-major operand without swizzle: 8-row x 16-byte core matrices, 1024 bytes
+// between core matrices along K (64 rows of N), 128 bytes between them along N
+QI u64 bdesc(u32 addr) { return (u64)((addr >> 4) & 0x3FFFu) | ((u64)(1024u >> 4) << 16) | ((u64)(128u >> 4) << 32) | ((u64)1 << 46); }
+#define R16(v) "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])), \
+    "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), \
+    "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])), \
+    "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+QI void tst16(u32 ta, const float (&v)[16]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+                 :: "r"(ta), R16(v) : "memory");
+}
+QI void tld32(u32 ta, float (&a)[16], float (&b)[16]) {
+    u32 r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                   "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(ta) : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) { a[j] = __uint_as_float(r[j]); b[j] = __uint_as_float(r[16 + j]); }
+}
+QI void tld16(u32 ta, u32 (&r)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(ta) : "memory");
+}
+// x[j] = D[:, c + j] + D[:, c + 32 + j] (head products + products with the matrix tails)
+QI void tld_pair(u32 ta, float (&x)[16]) {
+    u32 p[16], q[16];
+    tld16(ta, p);
+    tld16(ta + 32u, q);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) x[j] = __uint_as_float(p[j]) + __uint_as_float(q[j]);
+}
+QI void tld_sum(u32 ta, float (&a)[16], float (&b)[16]) {
+    tld_pair(ta, a);
+    tld_pair(ta + 16u, b);
+}
+QI void tst8(u32 ta, const float *v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 :: "r"(ta), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                    "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                    "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])) : "memory");
+}
+// the 16 values as TF32 heads at column ta and tails at column ta + lo (this warp's lanes), 8 at a time
+QI void put_split(u32 ta, u32 lo, const float (&x)[16]) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        float h[8], l[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) { h[j] = tf32r(x[8 * c + j]); l[j] = tf32r(x[8 * c + j] - h[j]); }
+        tst8(ta + 8u * c, h);
+        tst8(ta + lo + 8u * c, l);
+    }
+}
+// thread index read afresh (keeps per-stage offsets from being hoisted into registers)
+QI u32 tid_now() { u32 t; asm volatile("mov.u32 %0, %%tid.x;" : "=r"(t)); return t; }
+QI void mma_tf32(u32 d, u32 a, u64 b, u32 idesc, u32 acc) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, q;\n\t}"
+                 :: "r"(d), "r"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+// sum of v over the CTA (nw warps), every thread gets it; red: nw floats of shared memory
+QI float cta_sum(float v, float *red, u32 tid, u32 nw) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((tid & 31u) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    float s = 0.f;
+    for (u32 w = 0; w < nw; ++w) s += red[w];
+    return s;
+}
+// bounded wait for the completion of mbarrier phase `parity`
+QI bool mbar_wait(u32 bar, u32 parity, u32 limit) {
+    for (u32 it = 0; it < limit; ++it) {
+        u32 ok;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+)PRELUDE";
+
+uint32_t swz_tc(uint32_t l) { return l ^ (((l >> 4) ^ (l >> 8)) & 15u); }
+
+// Dynamic shared memory of a tensor-core pass: the transpose words, then 8 KB
+// per matrix slot; at least enough that no more CTAs fit on an SM than tensor
+// memory serves (512 columns: four CTAs of 2^11 tiles, two of 2^12).
+size_t tc_smem(const plan::Pass &p)
+{
+    const size_t need = (size_t(8) << p.k) + (p.tcm.size() / plan::kTcSlot) * 8192;
+    const size_t floor_bytes = p.k == 12 ? 78848 : 47104;
+    return std::max(need, floor_bytes);
+}
+int tc_cols(int k) { return k == 12 ? 256 : 128; }
+
+// Host packing of a pass's matrix slots: per slot one 64 x 32 K-major operand,
+// rows n < 32 the TF32 heads and rows 32 + n the tails of row n of the real form
+// [[Re, -Im], [Im, Re]] (element (n, kk) at byte (kk/4)*1024 + (n/8)*128 +
+// (n%8)*16 + (kk%4)*4). One product with N = 64 gives heads and tails of the
+// matrix at once; a product with N = 32 reads the heads alone.
+float tf32_round_host(float f)
+{
+    uint32_t b;
+    std::memcpy(&b, &f, 4);
+    if ((b & 0x7F800000u) != 0x7F800000u) b = (b + 0x1000u) & 0xFFFFE000u;
+    float r;
+    std::memcpy(&r, &b, 4);
+    return r;
+}
+
+void pack_tc_mats(const plan::Pass &p, std::vector<float> &out)
+{
+    const size_t nslot = p.tcm.size() / plan::kTcSlot;
+    out.assign(nslot * 2048, 0.f);
+    auto at = [](int n, int kk) { return size_t((kk / 4) * 256 + (n / 8) * 32 + (n % 8) * 4 + (kk % 4)); };
+    for (size_t sl = 0; sl < nslot; ++sl) {
+        const cd *G = p.tcm.data() + sl * plan::kTcSlot;
+        float *B = out.data() + sl * 2048;
+        for (int n = 0; n < 32; ++n)
+            for (int kk = 0; kk < 32; ++kk) {
+                const cd z = G[16 * (n & 15) + (kk & 15)];
+                const double x = (n < 16) == (kk < 16) ? z.real() : (n < 16 ? -z.imag() : z.imag());
+                const float h = tf32_round_host(float(x));
+                const float l = tf32_round_host(float(x - double(h)));
+                B[at(n, kk)] = h;
+                B[at(32 + n, kk)] = l;
+            }
+    }
+}
+
+std::string gen_source_tc(const plan::Pass &p)
+{
+    const int K = p.k, T = 1 << (K - kRegBits), NG = T / 128, NQ = K - kRegBits;
+    PassGeom G{K, NQ, K - kChunkBits, &p};
+    const int cols = tc_cols(K);
+    auto col_hi = [&](int g) { return 32 * g; };
+    auto col_d = [&](int g) { return 64 * NG + 64 * g; };
+    auto reg_off = [&](const int8_t *P, int j) {
+        uint32_t l = 0;
+        for (int b = 0; b < kRegBits; ++b)
+            if ((j >> b) & 1) l |= 1u << P[b];
+        return l;
+    };
+    auto phys_mask = [&](const int8_t *Q) {
+        std::vector<uint64_t> m(NQ);
+        for (int b = 0; b < NQ; ++b) m[b] = G.phys(1u << Q[b]);
+        return m;
+    };
+    auto word_mask = [&](const int8_t *Q) {
+        std::vector<uint64_t> m(NQ);
+        for (int b = 0; b < NQ; ++b) m[b] = swz_tc(1u << Q[b]);
+        return m;
+    };
+    const plan::Stage &s0 = p.stages.front(), &sl = p.stages.back();
+    const int nslot = int(p.tcm.size() / plan::kTcSlot);
+    // instruction descriptors: D FP32, A and B TF32, both K-major, M = 128, N = 64 / 32
+    const uint32_t idesc64 = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+    const uint32_t idesc32 = (1u << 4) | (2u << 7) | (2u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+    std::ostringstream o;
+    o << kPreludeTc;
+    o << "extern \"C\" __global__ void __launch_bounds__(" << T << ", " << (K == 12 ? 2 : 4)
+      << ") qv_tc(float2 *__restrict__ amp, u64 ntiles, const float4 *__restrict__ mats, int *status, u32 spin)\n{\n";
+    o << "    extern __shared__ __align__(1024) unsigned char smx[];\n";
+    o << "    __shared__ __align__(8) u64 mbar;\n    __shared__ u32 tslot;\n    __shared__ int s_abort;\n";
+    if (p.tc_unitary) o << "    __shared__ float red[2][" << T / 32 << "];\n";
+    o << "    float2 *tw = reinterpret_cast<float2 *>(smx);\n";
+    o << "    const u32 mb = smem_u32(smx + " << (8 << K) << ");\n";
+    o << "    const u32 tid = threadIdx.x, warp = tid >> 5;\n";
+    o << "    if (warp == 0) {\n"
+         "        asm volatile(\"tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\" :: \"r\"(smem_u32(&tslot)), \"r\"("
+      << cols << ") : \"memory\");\n"
+         "        asm volatile(\"tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\" ::: \"memory\");\n    }\n";
+    o << "    if (tid == 0) {\n"
+         "        asm volatile(\"mbarrier.init.shared::cta.b64 [%0], 1;\" :: \"r\"(smem_u32(&mbar)) : \"memory\");\n"
+         "        asm volatile(\"fence.mbarrier_init.release.cluster;\" ::: \"memory\");\n"
+         "        s_abort = 0;\n    }\n";
+    o << "    for (u32 i = tid; i < " << nslot * 512 << "u; i += " << T
+      << "u) reinterpret_cast<float4 *>(smx + " << (8 << K) << ")[i] = __ldg(mats + i);\n";
+    o << "    asm volatile(\"fence.proxy.async.shared::cta;\" ::: \"memory\");\n";
+    o << "    asm volatile(\"tcgen05.fence::before_thread_sync;\" ::: \"memory\");\n    __syncthreads();\n";
+    o << "    asm volatile(\"tcgen05.fence::after_thread_sync;\" ::: \"memory\");\n";
+    o << "    const u32 tm = tslot, bar = smem_u32(&mbar);\n";
+    o << "    const u32 lb = ((warp & 3u) * 32u) << 16, grp = warp >> 2;\n";
+    o << "    const u32 ahi = tm + lb + 32u * grp, dcol = tm + lb + " << col_d(0) << "u + 64u * grp;\n";
+    o << "    u32 phase = 0;\n";
+    o << "    const u64 gL = " << thread_expr(phys_mask(s0.in.Q), true) << ";\n";
+    o << "    const u64 gS = " << thread_expr(phys_mask(sl.out.Q), true) << ";\n";
+    o << "    float2 nx[16];\n";
+    o << "    if (blockIdx.x < ntiles) { const float2 *a = amp + ((" << tile_base_expr(p, "(u64)blockIdx.x") << ") + gL);\n";
+    for (int j = 0; j < 16; ++j) o << "      nx[" << j << "] = a[" << hex64(G.phys(reg_off(s0.in.P, j))) << "];\n";
+    o << "    }\n";
+    o << "    for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {\n";
+    o << "    const u64 base = " << tile_base_expr(p, "t") << ";\n";
+    o << "    float re[16], im[16];\n";
+    o << "#pragma unroll\n    for (int j = 0; j < 16; ++j) { re[j] = nx[j].x; im[j] = nx[j].y; }\n";
+    if (p.tc_unitary) {
+        o << "    float nin = 0.f;\n";
+        o << "#pragma unroll\n    for (int j = 0; j < 16; ++j) nin = fmaf(re[j], re[j], fmaf(im[j], im[j], nin));\n";
+    }
+    o << "    { const u64 tn = t + gridDim.x;\n";
+    o << "      if (tn < ntiles) { const float2 *a = amp + ((" << tile_base_expr(p, "tn") << ") + gL);\n";
+    for (int j = 0; j < 16; ++j) o << "        nx[" << j << "] = a[" << hex64(G.phys(reg_off(s0.in.P, j))) << "];\n";
+    o << "      }\n    }\n";
+    for (size_t s = 0; s < p.stages.size(); ++s) {
+        const plan::Stage &st = p.stages[s];
+        if (s > 0) {
+            const plan::Stage &pr = p.stages[s - 1];
+            o << "    {\n";
+            {
+                std::string wW = thread_expr(word_mask(pr.out.Q), false), wR = thread_expr(word_mask(st.in.Q), false);
+                for (std::string *e : {&wW, &wR})
+                    for (size_t q = e->find("tid"); q != std::string::npos; q = e->find("tid", q + 2)) e->replace(q, 3, "tn");
+                o << "      u32 tn = tid_now(); const u32 wW" << s << " = " << wW << ";\n";
+                o << "      tn = tid_now(); const u32 wR" << s << " = " << wR << ";\n";
+            }
+            for (int j = 0; j < 16; ++j)
+                o << "      tw[wW" << s << " ^ " << hex32(swz_tc(reg_off(pr.out.P, j))) << "] = make_float2(re[" << j
+                  << "], im[" << j << "]);\n";
+            o << "      __syncthreads();\n";
+            for (int j = 0; j < 16; ++j)
+                o << "      { const float2 w = tw[wR" << s << " ^ " << hex32(swz_tc(reg_off(st.in.P, j))) << "]; re[" << j
+                  << "] = w.x; im[" << j << "] = w.y; }\n";
+            if (st.mat < 0) o << "      __syncthreads();\n";
+            o << "    }\n";
+        }
+        if (st.mat < 0) continue;
+        o << "    {\n";
+        o << "      put_split(ahi, " << 32 * NG << "u, re);\n      put_split(ahi + 16u, " << 32 * NG << "u, im);\n";
+        o << "      asm volatile(\"tcgen05.wait::st.sync.aligned;\" ::: \"memory\");\n";
+        o << "      asm volatile(\"tcgen05.fence::before_thread_sync;\" ::: \"memory\");\n";
+        o << "      __syncthreads();\n";
+        o << "      if (s_abort) goto done;\n";
+        o << "      if (tid == 0) {\n";
+        o << "        asm volatile(\"tcgen05.fence::after_thread_sync;\" ::: \"memory\");\n";
+        if (st.ext >= 0)
+            o << "        const u32 slot = " << st.mat << "u + (u32)((base >> " << st.ext << ") & 1ull);\n";
+        else
+            o << "        const u32 slot = " << st.mat << "u;\n";
+        o << "        const u32 bm = mb + slot * 8192u;\n";
+        // D[:, 0:64] = A_hi [B_hi | B_lo], then D[:, 0:32] += A_lo B_hi
+        for (int g = 0; g < NG; ++g)
+            for (int pr = 0; pr < 2; ++pr)
+                for (int ks = 0; ks < 4; ++ks) {
+                    const int acol = col_hi(g) + (pr == 1 ? 32 * NG : 0) + 8 * ks;
+                    o << "        mma_tf32(tm + " << col_d(g) << "u, tm + " << acol << "u, bdesc(bm + " << 2048 * ks << "u), "
+                      << hex32(pr == 0 ? idesc64 : idesc32) << ", " << ((pr | ks) ? 1 : 0) << "u);\n";
+                }
+        o << "        asm volatile(\"tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\" :: \"r\"(bar) : \"memory\");\n";
+        o << "      }\n";
+        o << "      if (!mbar_wait(bar, phase, spin)) { s_abort = 1; atomicCAS(status, 0, 4); }\n";
+        o << "      phase ^= 1u;\n";
+        o << "      asm volatile(\"tcgen05.fence::after_thread_sync;\" ::: \"memory\");\n";
+        o << "      tld_sum(dcol, re, im);\n";
+        o << "    }\n";
+    }
+    if (p.tc_unitary) {
+        // The pass is a unitary acting inside each tile, so the tile keeps its
+        // norm; the tensor cores truncate their FP32 sums, which shrinks every
+        // stage's output by a few units in the last place. Rescaling the tile to
+        // its input norm removes that systematic part of the rounding error.
+        o << "    {\n";
+        o << "      float nout = 0.f;\n";
+        o << "#pragma unroll\n      for (int j = 0; j < 16; ++j) nout = fmaf(re[j], re[j], fmaf(im[j], im[j], nout));\n";
+        o << "      const float si = cta_sum(nin, red[0], tid, " << T / 32 << "u), so = cta_sum(nout, red[1], tid, " << T / 32
+          << "u);\n";
+        o << "      const float f = so > 0.f ? sqrtf(si / so) : 1.f;\n";
+        o << "#pragma unroll\n      for (int j = 0; j < 16; ++j) { re[j] *= f; im[j] *= f; }\n";
+        o << "    }\n";
+    }
+    o << "    { float2 *a = amp + (base + gS);\n";
+    for (int j = 0; j < 16; ++j)
+        o << "      a[" << hex64(G.phys(reg_off(sl.out.P, j))) << "] = make_float2(re[" << j << "], im[" << j << "]);\n";
+    o << "    }\n";
+    o << "    }\n";
+    o << "done:\n";
+    o << "    asm volatile(\"tcgen05.fence::before_thread_sync;\" ::: \"memory\");\n    __syncthreads();\n";
+    o << "    if (warp == 0) asm volatile(\"tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\" :: \"r\"(tm), \"r\"(" << cols
+      << ") : \"memory\");\n";
+    o << "}\n";
+    return o.str();
+}
+
 std::string gen_source(const plan::Pass &p, bool c64)
 {
     PassGeom G{p.k, p.k - kRegBits, p.k - kChunkBits, &p};
@@ -1024,7 +1334,7 @@ bool jit_available(std::string *why)
     return N.ok;
 }
 
-std::string jit_pass_source(const plan::Pass &p, bool c64) { return gen_source(p, c64); }
+std::string jit_pass_source(const plan::Pass &p, bool c64) { return p.tc ? gen_source_tc(p) : gen_source(p, c64); }
 
 namespace {
 // The number before `key` in a ptxas -v report ("Used 128 registers",
@@ -1050,7 +1360,7 @@ qv_status jit_compile_host(const std::vector<plan::Pass> &passes, bool c64, int6
     std::vector<char> ok(np, 0);
     int64_t bytes = 0;
     for (size_t i = 0; i < np; ++i) {
-        srcs[i] = gen_source(passes[i], c64);
+        srcs[i] = jit_pass_source(passes[i], c64);
         bytes += int64_t(srcs[i].size());
     }
     const size_t nt = std::max<size_t>(1, std::min<size_t>(np, std::max(1u, std::thread::hardware_concurrency())));
@@ -1132,13 +1442,23 @@ qv_status get_kernels(qv_state *s, const std::vector<std::string> &srcs, const c
             r = A.get_function(&c->fn, c->mod, entry);
             if (r != CUDA_SUCCESS) return cu_fail(r, "cuModuleGetFunction");
             c->smem = smem[todo[j]];
-            if (c->smem > 48 * 1024) {
-                r = A.set_attr(c->fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, int(c->smem));
-                if (r != CUDA_SUCCESS) return cu_fail(r, "cuFuncSetAttribute");
-            }
+            // the default limit (48 KB minus the static shared memory) can be below
+            // what a pass needs even at 48 KB: always raise it to the pass's size
+            r = A.set_attr(c->fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, int(c->smem));
+            if (r != CUDA_SUCCESS) return cu_fail(r, "cuFuncSetAttribute");
             r = A.occupancy(&c->per_sm, c->fn, threads[todo[j]], c->smem);
             if (r != CUDA_SUCCESS) return cu_fail(r, "cuOccupancyMaxActiveBlocksPerMultiprocessor");
-            if (c->per_sm < 1) return fail(QV_ERR_UNSUPPORTED, "compiled pass does not fit on an SM");
+            if (c->per_sm < 1) {
+                int regs = -1, st = -1, maxdyn = -1, maxthr = -1;
+                A.get_attr(&regs, CU_FUNC_ATTRIBUTE_NUM_REGS, c->fn);
+                A.get_attr(&st, CU_FUNC_ATTRIBUTE_SHARED_SIZE_BYTES, c->fn);
+                A.get_attr(&maxdyn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, c->fn);
+                A.get_attr(&maxthr, CU_FUNC_ATTRIBUTE_MAX_THREADS_PER_BLOCK, c->fn);
+                return fail(QV_ERR_UNSUPPORTED,
+                            "compiled pass does not fit on an SM (%d threads, %d registers, %d + %zu bytes of shared "
+                            "memory, at most %d dynamic, %d threads per CTA)",
+                            threads[todo[j]], regs, st, c->smem, maxdyn, maxthr);
+            }
             g_cache[{s->device, srcs[todo[j]]}] = c;
         }
         for (size_t i = 0; i < srcs.size(); ++i)
@@ -1154,10 +1474,63 @@ struct JitProgram {
     std::vector<std::vector<uint64_t>> args;  // by-value kernel parameter of each pass
     std::vector<int> threads;
     std::vector<uint64_t> ntiles;
+    // tensor-core passes: matrix slots of every pass in one device buffer
+    bool tc = false;
+    int device = 0;
+    void *mats = nullptr;
+    std::vector<size_t> mat_off;  // byte offset of each pass's slots
+    ~JitProgram()
+    {
+        if (mats) {
+            int cur = 0;
+            cudaGetDevice(&cur);
+            cudaSetDevice(device);
+            cudaFree(mats);
+            cudaSetDevice(cur);
+        }
+    }
 };
+
+namespace {
+qv_status jit_prepare_tc(qv_state *s, const std::vector<plan::Pass> &passes, std::shared_ptr<JitProgram> &out)
+{
+    if (s->dt != QV_C64) return fail(QV_ERR_UNSUPPORTED, "tensor-core passes are complex64 only");
+    auto P = std::make_shared<JitProgram>();
+    P->tc = true;
+    P->device = s->device;
+    std::vector<std::string> srcs(passes.size());
+    std::vector<size_t> smem(passes.size());
+    std::vector<float> all, one;
+    P->threads.resize(passes.size());
+    for (size_t i = 0; i < passes.size(); ++i) {
+        srcs[i] = gen_source_tc(passes[i]);
+        smem[i] = tc_smem(passes[i]);
+        P->threads[i] = 1 << (passes[i].k - kRegBits);
+        P->ntiles.push_back(dim(s) >> passes[i].k);
+        pack_tc_mats(passes[i], one);
+        P->mat_off.push_back(all.size() * sizeof(float));
+        all.insert(all.end(), one.begin(), one.end());
+        P->args.emplace_back();
+    }
+    QV_TRY(get_kernels(s, srcs, "qv_tc", smem, P->threads, P->fns));
+    for (const auto &f : P->fns) {
+        // at most as many CTAs per SM as tensor memory serves
+        const int cap = 512 / tc_cols(passes[size_t(&f - &P->fns[0])].k);
+        if (f->per_sm > cap) return fail(QV_ERR_UNSUPPORTED, "tensor-core pass: %d CTAs per SM exceed tensor memory", f->per_sm);
+    }
+    QV_CUDA(cudaSetDevice(s->device));
+    if (!all.empty()) {
+        QV_CUDA(cudaMalloc(&P->mats, all.size() * sizeof(float)));
+        QV_TRY(copy_h2d(s, P->mats, all.data(), all.size() * sizeof(float)));
+    }
+    out = P;
+    return QV_OK;
+}
+}  // namespace
 
 qv_status jit_prepare(qv_state *s, const std::vector<plan::Pass> &passes, std::shared_ptr<JitProgram> &out)
 {
+    if (!passes.empty() && passes.front().tc) return jit_prepare_tc(s, passes, out);
     const bool c64 = s->dt == QV_C64;
     auto P = std::make_shared<JitProgram>();
     std::vector<std::string> srcs(passes.size());
@@ -1189,6 +1562,26 @@ qv_status jit_prepare(qv_state *s, const std::vector<plan::Pass> &passes, std::s
 qv_status jit_launch(qv_state *s, const JitProgram &P)
 {
     QV_CUDA(cudaSetDevice(s->device));
+    if (P.tc) {
+        int *status = nullptr;
+        QV_TRY(status_word(s, &status));
+        uint32_t spin = 1u << 22;
+        for (size_t i = 0; i < P.fns.size(); ++i) {
+            const Compiled &c = *P.fns[i];
+            uint64_t ntiles = P.ntiles[i];
+            const unsigned grid = unsigned(std::min<uint64_t>(ntiles, uint64_t(c.per_sm) * s->num_sms));
+            void *amp = s->amp;
+            void *mats = static_cast<char *>(P.mats) + P.mat_off[i];
+            void *args[] = {&amp, &ntiles, &mats, &status, &spin};
+            prof_bytes(s, QV_K_FUSED, 2.0 * double(dim(s)) * amp_bytes(s->dt));
+            prof_begin(s, QV_K_FUSED);
+            const CUresult r = api().launch(c.fn, grid, 1, 1, unsigned(P.threads[i]), 1, 1, unsigned(c.smem),
+                                            reinterpret_cast<CUstream>(s->stream), args, nullptr);
+            prof_end(s, QV_K_FUSED);
+            if (r != CUDA_SUCCESS) return cu_fail(r, "cuLaunchKernel");
+        }
+        return QV_OK;
+    }
     for (size_t i = 0; i < P.fns.size(); ++i) {
         const Compiled &c = *P.fns[i];
         uint64_t ntiles = P.ntiles[i];

@@ -321,6 +321,277 @@ void fuse_pair_blocks(Pass &P, bool pin0, int &pair_ops)
     P.stages = std::move(nst);
 }
 
+
+// ---------------------------------------------------------------- tensor-core stages
+// A stage's register set is a bitmask R over tile positions. A gate runs when
+// its non-diagonal target is a register position and its control (and a
+// diagonal target) is a register position or lies outside the tile; at most
+// one qubit outside the tile per stage (`ext`), whose value picks one of two
+// matrices for the whole tile.
+bool tc_exec(const PGate &g, const std::vector<int> &pos_of, uint32_t R, int &ext)
+{
+    if (g.cls == G_SWAP) return true;  // both qubits are tile positions (pass selection)
+    auto in_reg = [&](int q) { return pos_of[q] >= 0 && ((R >> pos_of[q]) & 1u); };
+    int need = -1;
+    if (!in_reg(g.t)) {
+        if (g.cls != G_DIAG || pos_of[g.t] >= 0) return false;
+        need = g.t;
+    }
+    if (g.c >= 0 && !in_reg(g.c)) {
+        if (pos_of[g.c] >= 0 || need >= 0) return false;
+        need = g.c;
+    }
+    if (need >= 0) {
+        if (ext == -2 || (ext >= 0 && ext != need)) return false;  // -2: no qubit outside allowed
+        ext = need;
+    }
+    return true;
+}
+
+inline uint32_t swap_bits(uint32_t R, int a, int b)
+{
+    const uint32_t x = ((R >> a) ^ (R >> b)) & 1u;
+    return R ^ ((x << a) | (x << b));
+}
+
+// Gates of `left` that would run (in order, with blocking) with register set R;
+// `ext_used` reports whether one needs a qubit outside the tile.
+int tc_count(const std::vector<PGate> &gates, const std::vector<int> &left, const std::vector<int> &pos_of, int n,
+             uint32_t R, size_t max_scan, bool *ext_used)
+{
+    std::vector<char> blocked(n, 0);
+    int cnt = 0, ext = -1;
+    for (size_t i = 0; i < left.size() && i < max_scan; ++i) {
+        const PGate &g = gates[left[i]];
+        int qs[3];
+        const int nq = qubits(g, qs);
+        bool blk = false;
+        for (int j = 0; j < nq; ++j) blk |= blocked[qs[j]] != 0;
+        if (!blk && tc_exec(g, pos_of, R, ext)) {
+            ++cnt;
+            if (g.cls == G_SWAP) R = swap_bits(R, pos_of[g.t], pos_of[g.t2]);
+        } else {
+            for (int j = 0; j < nq; ++j) blocked[qs[j]] = 1;
+        }
+    }
+    if (ext_used) *ext_used = ext >= 0;
+    return cnt;
+}
+
+// Layout with register bit j on the j-th set bit of R. Lanes: positions 0..4
+// when R holds none of them (the load/store layout); otherwise the first four
+// lanes take positions of distinct residues mod 4, so that a half warp's 8-byte
+// shared-memory words (word = swizzled position) fall in distinct banks.
+Layout tc_layout(int k, uint32_t R)
+{
+    Layout L;
+    int j = 0;
+    for (int p = 0; p < k; ++p)
+        if ((R >> p) & 1u) L.P[j++] = int8_t(p);
+    std::vector<int> rest;
+    for (int p = 0; p < k; ++p)
+        if (!((R >> p) & 1u)) rest.push_back(p);
+    std::vector<int> q;
+    if ((R & ((1u << kTcLanes) - 1)) == 0) {
+        q = rest;  // ascending: lanes on 0..4
+    } else {
+        std::vector<char> used(rest.size(), 0);
+        for (int res = 0; res < 4; ++res)
+            for (size_t i = 0; i < rest.size(); ++i)
+                if (!used[i] && rest[i] % 4 == res) {
+                    q.push_back(rest[i]);
+                    used[i] = 1;
+                    break;
+                }
+        for (size_t i = 0; i < rest.size(); ++i)
+            if (!used[i]) q.push_back(rest[i]);
+    }
+    for (int b = 0; b < k - kRegBits; ++b) L.Q[b] = int8_t(q[b]);
+    for (int b = k - kRegBits; b < kMaxK - kRegBits; ++b) L.Q[b] = -1;
+    return L;
+}
+
+bool tc_canonical(const Layout &L, int k)
+{
+    for (int b = 0; b < kTcLanes; ++b)
+        if (L.Q[b] != b) return false;
+    for (int j = 0; j < kRegBits; ++j)
+        if (L.P[j] < kTcLanes) return false;
+    (void)k;
+    return true;
+}
+
+int reg_bit(const Layout &L, int pos)
+{
+    for (int j = 0; j < kRegBits; ++j)
+        if (L.P[j] == pos) return j;
+    return -1;
+}
+
+// G <- M G for the 16x16 embedding M of gate g in register coordinates (target
+// register bit jt, control register bit jc, or -1). `v` is the value of the
+// stage's qubit outside the tile for this matrix variant; `ext` that qubit.
+void tc_mul_gate(cd G[kTcSlot], const PGate &g, int jt, int jc, int v, int ext)
+{
+    cd M[kTcSlot];
+    for (int e = 0; e < kTcSlot; ++e) M[e] = 0.0;
+    for (int c = 0; c < 16; ++c) {
+        bool on = true;
+        if (g.c >= 0) on = jc >= 0 ? ((c >> jc) & 1) != 0 : (g.c == ext && v == 1);
+        if (!on) {
+            M[16 * c + c] = 1.0;
+            continue;
+        }
+        if (jt < 0) {  // diagonal gate on the qubit outside the tile
+            M[16 * c + c] = g.U[(g.t == ext && v == 1) ? 3 : 0];
+            continue;
+        }
+        const int xt = (c >> jt) & 1;
+        for (int rt = 0; rt < 2; ++rt) {
+            const int r = (c & ~(1 << jt)) | (rt << jt);
+            M[16 * r + c] += g.U[2 * rt + xt];
+        }
+    }
+    cd T[kTcSlot];
+    for (int r = 0; r < 16; ++r)
+        for (int c = 0; c < 16; ++c) {
+            cd a = 0.0;
+            for (int m = 0; m < 16; ++m) a += M[16 * r + m] * G[16 * m + c];
+            T[16 * r + c] = a;
+        }
+    std::copy(T, T + kTcSlot, G);
+}
+
+uint32_t mask_of(const int8_t P[kRegBits])
+{
+    uint32_t m = 0;
+    for (int j = 0; j < kRegBits; ++j) m |= 1u << P[j];
+    return m;
+}
+
+// Stages of one tensor-core pass over the gates `left` (tile positions
+// pos_of). Runs gates until `left` is empty or the matrix slots are used up;
+// `left` keeps the gates that did not run.
+void build_tc_pass(const std::vector<PGate> &gates, std::vector<int> &left, const std::vector<int> &pos_of, int n, int k,
+                   Pass &P)
+{
+    const size_t scan_max = 2 * kLookahead;
+    const uint32_t low = (1u << kTcLanes) - 1;
+    const int max_slots = tc_max_slots(k);
+    auto best_set = [&](bool prefer_high, bool *ext_used) {
+        uint32_t best = 0, best_high = 0;
+        int bc = -1, bch = -1;
+        bool be = false, beh = false;
+        for (uint32_t R = 0; R < (1u << k); ++R) {
+            if (__builtin_popcount(R) != kRegBits) continue;
+            bool e = false;
+            const int c = tc_count(gates, left, pos_of, n, R, scan_max, &e);
+            if (c > bc) {
+                bc = c;
+                best = R;
+                be = e;
+            }
+            if (!(R & low) && c > bch) {
+                bch = c;
+                best_high = R;
+                beh = e;
+            }
+        }
+        // a first stage without lanes among its registers needs no transpose after the load
+        if (prefer_high && bch > 0 && 4 * bch >= 3 * bc) {
+            *ext_used = beh;
+            return best_high;
+        }
+        *ext_used = be;
+        return best;
+    };
+    std::vector<Stage> stages;
+    int slots = 0;
+    bool ext_used = false;
+    uint32_t R = best_set(true, &ext_used);
+    Layout L;
+    if (R & low) {  // load in a canonical layout, then transpose to R
+        uint32_t H = 0;
+        for (int p = k - 1, c = 0; p >= kTcLanes && c < kRegBits; --p, ++c) H |= 1u << p;
+        const Layout C = tc_layout(k, H);
+        stages.push_back(Stage{C, C, 0, 0, -1, -1});
+    }
+    L = tc_layout(k, R);
+    while (!left.empty()) {
+        if (slots + 1 > max_slots) break;
+        const bool allow_ext = slots + 2 <= max_slots;
+        Stage st{L, L, 0, 0, slots, -1};
+        cd G[2][kTcSlot];
+        for (int v = 0; v < 2; ++v)
+            for (int e = 0; e < kTcSlot; ++e) G[v][e] = (e % 17 == 0) ? cd(1.0) : cd(0.0);
+        std::vector<int> still;
+        std::vector<char> blocked(n, 0);
+        int ext = allow_ext ? -1 : -2, ran = 0;
+        for (int gi : left) {
+            const PGate &g = gates[gi];
+            int qs[3];
+            const int nq = qubits(g, qs);
+            bool blk = false;
+            for (int j = 0; j < nq; ++j) blk |= blocked[qs[j]] != 0;
+            if (!blk && tc_exec(g, pos_of, mask_of(L.P), ext)) {
+                ++ran;
+                if (g.cls == G_SWAP) {
+                    const int a = pos_of[g.t], b = pos_of[g.t2];
+                    for (int j = 0; j < kRegBits; ++j) L.P[j] = int8_t(L.P[j] == a ? b : L.P[j] == b ? a : L.P[j]);
+                    for (int q = 0; q < k - kRegBits; ++q) L.Q[q] = int8_t(L.Q[q] == a ? b : L.Q[q] == b ? a : L.Q[q]);
+                    continue;
+                }
+                const int jt = pos_of[g.t] >= 0 ? reg_bit(L, pos_of[g.t]) : -1;
+                const int jc = (g.c >= 0 && pos_of[g.c] >= 0) ? reg_bit(L, pos_of[g.c]) : -1;
+                for (int v = 0; v < 2; ++v) tc_mul_gate(G[v], g, jt, jc, v, ext);
+            } else {
+                still.push_back(gi);
+                for (int j = 0; j < nq; ++j) blocked[qs[j]] = 1;
+            }
+        }
+        left.swap(still);
+        st.out = L;
+        if (ran == 0) break;  // the frontier needs a qubit outside the tile and no slot is left for it
+        st.ext = ext >= 0 ? ext : -1;
+        const int nv = ext >= 0 ? 2 : 1;
+        for (int v = 0; v < nv; ++v) P.tcm.insert(P.tcm.end(), G[v], G[v] + kTcSlot);
+        slots += nv;
+        stages.push_back(st);
+        if (left.empty()) break;
+        R = best_set(false, &ext_used);
+        L = tc_layout(k, R);
+    }
+    L = stages.back().out;
+    if (!tc_canonical(L, k)) {
+        uint32_t H = 0;
+        int c = 0;
+        for (int j = 0; j < kRegBits; ++j)
+            if (L.P[j] >= kTcLanes) {
+                H |= 1u << L.P[j];
+                ++c;
+            }
+        for (int p = k - 1; p >= kTcLanes && c < kRegBits; --p)
+            if (!((H >> p) & 1u)) {
+                H |= 1u << p;
+                ++c;
+            }
+        const Layout C = tc_layout(k, H);
+        stages.push_back(Stage{C, C, 0, 0, -1, -1});
+    }
+    P.stages = std::move(stages);
+    P.tc = true;
+    P.tc_unitary = true;
+    for (size_t sl = 0; sl < P.tcm.size() / kTcSlot; ++sl) {
+        const cd *G = P.tcm.data() + sl * kTcSlot;
+        for (int r = 0; r < 16; ++r)
+            for (int c = 0; c < 16; ++c) {
+                cd a = 0.0;
+                for (int m = 0; m < 16; ++m) a += std::conj(G[16 * m + r]) * G[16 * m + c];
+                if (std::abs(a - (r == c ? 1.0 : 0.0)) > 1e-12) P.tc_unitary = false;
+            }
+    }
+}
+
 }  // namespace
 
 double fma_per_amp_c64(const Op &op)
@@ -342,13 +613,20 @@ int classify(const std::complex<double> U[4])
 }
 
 bool make_plan(int n, int k, bool pin0, bool fuse, bool pairs, const std::vector<PGate> &gates,
-               std::vector<Pass> &out, PlanStats &stats, std::string &err)
+               std::vector<Pass> &out, PlanStats &stats, std::string &err, bool tc)
 {
     out.clear();
     stats = PlanStats{};
     if (k < kMinK || k > kMaxK || k > n) {
         err = "tile size out of range";
         return false;
+    }
+    if (tc) {
+        if (k < 11) {
+            err = "tensor-core passes need tiles of 2^11 or 2^12 amplitudes";
+            return false;
+        }
+        pin0 = false;
     }
     const int nh = k - kChunkBits;
     if (pin0) {
@@ -373,7 +651,7 @@ bool make_plan(int n, int k, bool pin0, bool fuse, bool pairs, const std::vector
                     ex.push_back(g);
                 }
             }
-            return make_plan(n, k, pin0, fuse, pairs, ex, out, stats, err);
+            return make_plan(n, k, pin0, fuse, pairs, ex, out, stats, err, tc);
         }
     }
     std::vector<int> rem(gates.size());
@@ -386,9 +664,19 @@ bool make_plan(int n, int k, bool pin0, bool fuse, bool pairs, const std::vector
     while (!rem.empty()) {
         // ---- choose the tile's high qubits greedily
         std::vector<char> inS(n, 0);
+        // tensor-core stages take one qubit outside the tile per gate at most: a
+        // controlled diagonal gate needs its target in the tile
+        auto need_of = [&](const PGate &g, int need[2]) {
+            const int nn = needs(g, need);
+            if (tc && nn == 0 && g.cls == G_DIAG && g.c >= 0) {
+                need[0] = g.t;
+                return 1;
+            }
+            return nn;
+        };
         auto fits = [&](const PGate &g) {
             int need[2];
-            const int nn = needs(g, need);
+            const int nn = need_of(g, need);
             for (int i = 0; i < nn; ++i)
                 if (!inS[need[i]]) return false;
             return true;
@@ -402,7 +690,7 @@ bool make_plan(int n, int k, bool pin0, bool fuse, bool pairs, const std::vector
             int steps = nh;
             if (attempt == 1) {
                 int need[2];
-                const int nn = needs(gates[rem[0]], need);
+                const int nn = need_of(gates[rem[0]], need);
                 for (int i = 0; i < nn; ++i)
                     if (!inS[need[i]]) {
                         inS[need[i]] = 1;
@@ -420,7 +708,7 @@ bool make_plan(int n, int k, bool pin0, bool fuse, bool pairs, const std::vector
                     int soon = 0;  // tie-break: gates needing q soon
                     for (size_t r = 0; r < rem.size() && r < size_t(kLookahead); ++r) {
                         int need[2];
-                        const int nn = needs(gates[rem[r]], need);
+                        const int nn = need_of(gates[rem[r]], need);
                         for (int i = 0; i < nn; ++i) soon += need[i] == q;
                     }
                     const long long score = (long long)cnt * 4096 + soon * 16 + (n - q);
@@ -475,6 +763,34 @@ bool make_plan(int n, int k, bool pin0, bool fuse, bool pairs, const std::vector
         }
         std::vector<int> pg;
         for (int r : taken) pg.push_back(rem[r]);
+        if (tc) {
+            std::vector<int> left = pg;
+            build_tc_pass(gates, left, pos_of, n, k, P);
+            if (left.size() == pg.size()) {
+                err = "planner made no progress";
+                return false;
+            }
+            std::vector<char> done(gates.size(), 0);
+            for (int gi : pg) done[gi] = 1;
+            for (int gi : left) done[gi] = 0;
+            std::vector<int> nrem;
+            for (int gi : rem)
+                if (!done[gi]) nrem.push_back(gi);
+            P.ngates = int(pg.size() - left.size());
+            stats.passes++;
+            stats.stages += int(P.stages.size());
+            stats.transposes += int(P.stages.size()) - 1;
+            stats.gates += P.ngates;
+            for (const Stage &st : P.stages)
+                if (st.mat >= 0) {
+                    stats.tc_mats++;
+                    // 16 complex multiply-adds per amplitude and stage (8 real operations each)
+                    stats.flops_per_amp += 128.0;
+                }
+            out.push_back(std::move(P));
+            rem.swap(nrem);
+            continue;
+        }
 
         // ---- stages: run gates whose target is a register bit; transpose otherwise
         LayoutState ls{k, {}};

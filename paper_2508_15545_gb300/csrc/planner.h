@@ -83,6 +83,10 @@ struct Stage {
     Layout in;        // layout the registers are read in (after the transpose)
     Layout out;       // layout at the end of the stage (SWAPs relabel positions)
     int op_begin, op_end;
+    // Tensor-core plans only: first slot of this stage's 16x16 matrix in
+    // Pass::tcm (-1: a transpose-only stage) and the physical qubit outside the
+    // tile whose value selects slot mat + 1 instead of mat (-1: none).
+    int mat = -1, ext = -1;
 };
 
 struct Pass {
@@ -94,10 +98,25 @@ struct Pass {
     std::vector<Stage> stages;
     std::vector<Op> ops;
     int ngates = 0;
+    // Tensor-core plans: every stage applies one dense 16x16 complex matrix to
+    // the 16 amplitudes that differ in its four register positions (register
+    // bit j <-> index bit j, row-major, out = M in); tcm holds kTcSlot entries
+    // per matrix slot.
+    bool tc = false;
+    std::vector<std::complex<double>> tcm;
+    // every matrix of the pass is unitary (to 1e-12): the pass then keeps the
+    // norm of every tile, since it acts inside tiles
+    bool tc_unitary = false;
 };
+
+constexpr int kTcSlot = 256;
+constexpr int kTcLanes = 5;  // tensor-core load/store layouts: lane b <-> tile position b
+// Matrix slots a tensor-core pass may hold (shared memory: 8 KB each).
+inline int tc_max_slots(int k) { return k >= 12 ? 8 : 7; }
 
 struct PlanStats {
     int passes = 0, stages = 0, transposes = 0, gates = 0, ops = 0, pair_ops = 0;
+    int tc_mats = 0;  // tensor-core plans: stages that apply a matrix
     // algorithmic floating-point operations per amplitude of the state, summed
     // over all ops: a 2x2 complex matrix on a pair is 28 real operations (14 per
     // amplitude), a diagonal one 6 per amplitude, X none, a 4x4 on a group of
@@ -117,8 +136,16 @@ struct PlanStats {
 // `fuse` = false keeps one op per gate. `pairs` (with `fuse`) then merges runs
 // of ops that act only on two register bits (targets and register selects; not
 // the packed lane bit) into GEN2 ops where that takes fewer FP32 operations.
+//
+// `tc` plans for the tensor-core kernel instead (k >= 11, 8-byte amplitudes;
+// pin0, fuse and pairs are ignored): a stage holds any four tile positions in
+// registers and runs, in order, every gate whose qubits are all register
+// positions, except that a control or a diagonal target may lie outside the
+// tile (one such qubit per stage: it selects one of two matrices per tile).
+// The stage's gates multiply into one 16x16 matrix. Load and store layouts put
+// lanes on tile positions 0..4 and registers on positions >= 5.
 bool make_plan(int n, int k, bool pin0, bool fuse, bool pairs, const std::vector<PGate> &gates,
-               std::vector<Pass> &out, PlanStats &stats, std::string &err);
+               std::vector<Pass> &out, PlanStats &stats, std::string &err, bool tc = false);
 
 // FP32 fused multiply-adds per amplitude the compiled complex64 kernel spends
 // on `op` (the cost model of the pair fusion).

@@ -413,6 +413,14 @@ qv_status qv_plan_source(int n, qv_dtype dt, const qv_gate *g, size_t ng, const 
     return QV_OK;
 }
 
+qv_status qv_plan_tc_stage(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t pass,
+                           int32_t stage, qv_tc_stage *out)
+{
+    if (!out) return fail(QV_ERR_ARG, "out is NULL");
+    QV_TRY(check_plan_args(n, dt, g, ng));
+    return plan_tc_stage(n, dt, g, ng, opts, pass, stage, out);
+}
+
 qv_status qv_plan_compile(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int64_t out[4])
 {
     if (!out) return fail(QV_ERR_ARG, "out is NULL");

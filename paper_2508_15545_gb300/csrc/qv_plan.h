@@ -23,6 +23,9 @@ qv_status plan_info(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_pl
 qv_status plan_source(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int pass,
                       std::string &src);
 qv_status plan_compile(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int64_t out[4]);
+// Host only: one stage of a tensor-core plan (qv_plan_tc_stage).
+qv_status plan_tc_stage(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int pass,
+                        int stage, qv_tc_stage *out);
 
 // Bit q of every index moves to bit perm[q].
 qv_status apply_permutation(qv_state *s, const int32_t *perm);

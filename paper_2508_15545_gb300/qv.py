@@ -21,6 +21,7 @@ QV_MODE_AUTO, QV_MODE_PLAIN, QV_MODE_FUSED = 0, 1, 2
 QV_PLAN_NO_FUSION = 1
 QV_PLAN_INTERPRET = 2
 QV_PLAN_NO_PAIRS = 4
+QV_PLAN_TENSOR = 8
 QV_ALLOC_HOST = 1
 QV_SWEEP_AUTO, QV_SWEEP_PER_GATE, QV_SWEEP_TILES, QV_SWEEP_COMPILED = 0, 1, 2, 3
 STATUS_NAMES = {0: "QV_OK", 1: "QV_ERR_ARG", 2: "QV_ERR_OOM", 3: "QV_ERR_CUDA",
@@ -48,6 +49,13 @@ class qv_gate(ctypes.Structure):
 class qv_plan_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("tile_bits", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 5)]
+
+
+class qv_tc_stage(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("nstages", ctypes.c_int32), ("tile_qubit", ctypes.c_int32 * 12),
+                ("in_reg", ctypes.c_int32 * 4), ("in_thr", ctypes.c_int32 * 8),
+                ("out_reg", ctypes.c_int32 * 4), ("out_thr", ctypes.c_int32 * 8),
+                ("has_matrix", ctypes.c_int32), ("ext", ctypes.c_int32), ("m", (qv_c128 * 256) * 2)]
 
 
 class qv_kernel_stat(ctypes.Structure):
@@ -98,6 +106,8 @@ def _load():
                            ctypes.POINTER(ctypes.c_size_t)],
         "qv_plan_compile": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(qv_gate), ctypes.c_size_t,
                             ctypes.POINTER(qv_plan_opts), ctypes.POINTER(ctypes.c_int64)],
+        "qv_plan_tc_stage": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(qv_gate), ctypes.c_size_t,
+                             ctypes.POINTER(qv_plan_opts), ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(qv_tc_stage)],
         "qv_norm2": [_H, ctypes.POINTER(ctypes.c_double)],
         "qv_expect_z": [_H, P, P, ctypes.POINTER(ctypes.c_double)],
         "qv_expect_pauli": [_H, ctypes.POINTER(qv_pauli_term), ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)],
@@ -324,6 +334,25 @@ def qv_plan_compile(n: int, dtype: int, gates, tile_bits: int = 0, flags: int = 
     _check(lib.qv_plan_compile(n, dtype, arr, ng, ctypes.byref(opts), out))
     return {"passes": int(out[0]), "source_bytes": int(out[1]), "max_registers": int(out[2]),
             "spilling_passes": int(out[3])}
+
+
+def qv_plan_tc_stage(n: int, gates, pass_index: int, stage: int, tile_bits: int = 0, flags: int = 0) -> dict:
+    """Stage ``stage`` of pass ``pass_index`` of the tensor-core plan (host only):
+    layouts (tile positions of register and thread bits), the physical qubit of
+    every tile position, and the stage's 16x16 matrices."""
+    if isinstance(gates, tuple) and len(gates) == 2 and isinstance(gates[1], int):
+        arr, ng = gates
+    else:
+        arr, ng = gates_to_c(gates), len(gates)
+    opts = plan_opts(QV_MODE_FUSED, tile_bits, flags | QV_PLAN_TENSOR)
+    o = qv_tc_stage()
+    _check(lib.qv_plan_tc_stage(n, QV_C64, arr, ng, ctypes.byref(opts), pass_index, stage, ctypes.byref(o)))
+    k = int(o.k)
+    m = np.array([[complex(o.m[v][e].re, o.m[v][e].im) for e in range(256)] for v in range(2)]).reshape(2, 16, 16)
+    return {"k": k, "nstages": int(o.nstages), "tile_qubit": list(o.tile_qubit)[:k],
+            "in_reg": list(o.in_reg), "in_thr": list(o.in_thr)[:k - 4],
+            "out_reg": list(o.out_reg), "out_thr": list(o.out_thr)[:k - 4],
+            "has_matrix": bool(o.has_matrix), "ext": int(o.ext), "m": m}
 
 
 def qv_permute_qubits(h: int, perm: Sequence[int]):
