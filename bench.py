@@ -515,6 +515,58 @@ def extras(args, qv, torch, dev, h64, gates):
         qv.qv_destroy(hh)
     except Exception as e:  # noqa: BLE001
         res["host_memory_state"] = {"error": str(e)}
+    # 1d. the same step with the tensor-core engine (QV_PLAN_TENSOR, 2^12 tiles)
+    try:
+        garr = qv.gates_to_c(gates)
+
+        def tc_step():
+            qv.qv_set_basis(h64, 0)
+            qv.qv_apply_circuit(h64, (garr, len(gates)), qv.QV_MODE_FUSED, 12, qv.QV_PLAN_TENSOR)
+        ms_tc = _timed(torch, dev, tc_step, 2)
+        qv.qv_sync(h64)
+        info = qv.qv_plan_info(args.n, qv.QV_C64, (garr, len(gates)), 12, qv.QV_PLAN_TENSOR)
+        res["tensor_core_engine"] = {"tile_bits": 12, "ms_per_step": ms_tc,
+                                     "updates_per_s": len(gates) * N / (ms_tc / 1e3),
+                                     "passes": info["passes"], "stages": info["stages"], "matrix_stages": info["ops"],
+                                     "frac_of_measured_hbm": 2.0 * info["passes"] * N * 8 / (ms_tc / 1e3) / 1e9 / peak,
+                                     "norm2_after": qv.qv_norm2(h64)}
+    except Exception as e:  # noqa: BLE001
+        res["tensor_core_engine"] = {"error": str(e)}
+    # 1e. end to end through the API: the first call of a new circuit structure
+    # (planning + NVRTC of every pass + run), and a variational loop (new angles
+    # every step: planning again, compiled passes reused, coefficients uploaded)
+    try:
+        g41 = W.random_circuit(args.n, args.layers + 1, W.config_seed(1, 41))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        qv.qv_set_basis(h64, 0)
+        qv.qv_apply_circuit(h64, g41, qv.QV_MODE_FUSED)
+        qv.qv_expect_z(h64)
+        first_ms = (time.perf_counter() - t0) * 1e3
+        t0 = time.perf_counter()
+        qv.qv_set_basis(h64, 0)
+        qv.qv_apply_circuit(h64, g41, qv.QV_MODE_FUSED)
+        qv.qv_expect_z(h64)
+        again_ms = (time.perf_counter() - t0) * 1e3
+        steps_v = 3
+        t0 = time.perf_counter()
+        for v in range(steps_v):
+            gv = W.random_circuit(args.n, args.layers, W.config_seed(1, 500 + v))   # same structure, new angles
+            qv.qv_set_basis(h64, 0)
+            qv.qv_apply_circuit(h64, gv, qv.QV_MODE_FUSED)
+            qv.qv_expect_z(h64)
+        var_ms = (time.perf_counter() - t0) * 1e3 / steps_v
+        res["e2e_variants"] = {
+            "first_call_new_structure_ms": first_ms,
+            "same_call_again_ms": again_ms,
+            "first_call_note": "%d-layer circuit (%d gates) never planned or compiled in this process: planning, "
+                               "NVRTC of every pass, run, <Z_q> read-out" % (args.layers + 1, len(g41)),
+            "variational_ms_per_step": var_ms,
+            "variational_updates_per_s": len(gates) * N / (var_ms / 1e3),
+            "variational_note": "new angles every step (same structure): the plan is made again, the compiled "
+                                "passes are reused, coefficients go to the kernels as parameters"}
+    except Exception as e:  # noqa: BLE001
+        res["e2e_variants"] = {"error": str(e)}
     # 2. complex128 rerun of the bench circuit and its distance to the complex64 result
     try:
         free, _ = torch.cuda.mem_get_info(dev)
@@ -576,6 +628,44 @@ def extras(args, qv, torch, dev, h64, gates):
         qv.qv_destroy(ha)
     except Exception as e:  # noqa: BLE001
         res["adjoint_grad"] = {"error": str(e)}
+    # 3b. size sweep: the random-circuit recipe at 16..30 qubits (20 layers; 40 at five sizes),
+    # fused complex64, default tile size; the oracle on every host core beside it
+    try:
+        from oracle import oracle as O
+        othreads = O.set_threads(host_cores())
+        sweep = []
+        hs = None
+        for n_s, layers_s in [(n, 20) for n in range(16, 31)] + [(n, 40) for n in (16, 20, 24, 28, 30)]:
+            if n_s > args.n:
+                continue
+            gs = W.random_circuit(n_s, layers_s, W.config_seed(0, n_s))
+            arr = (qv.gates_to_c(gs), len(gs))
+            hs = qv.qv_create(n_s, qv.QV_C64)
+
+            def one():
+                qv.qv_set_basis(hs, 0)
+                qv.qv_apply_circuit(hs, arr, qv.QV_MODE_FUSED)
+            ms_s = _timed(torch, dev, one, 3 if n_s < 28 else 1)
+            passes = qv.qv_plan_info(n_s, qv.QV_C64, arr)["passes"]
+            row = {"n": n_s, "layers": layers_s, "gates": len(gs), "ms": ms_s,
+                   "updates_per_s": len(gs) * (1 << n_s) / (ms_s / 1e3), "passes": passes,
+                   "frac_of_measured_hbm": 2.0 * passes * (8 << n_s) / (ms_s / 1e3) / 1e9 / peak}
+            qv.qv_destroy(hs)
+            hs = None
+            # the oracle: the whole circuit up to 22 qubits, else its first 8 gates
+            ng_o = len(gs) if n_s <= 22 else 8
+            psi = O.basis(n_s, 0)
+            t0 = time.perf_counter()
+            O.run(n_s, gs[:ng_o], psi)
+            el = time.perf_counter() - t0
+            del psi
+            row["oracle_updates_per_s"] = ng_o * (1 << n_s) / el
+            row["oracle_sample"] = "%s on %d host threads" % ("whole circuit" if ng_o == len(gs) else "first 8 gates",
+                                                               othreads)
+            sweep.append(row)
+        res["size_sweep"] = sweep
+    except Exception as e:  # noqa: BLE001
+        res["size_sweep"] = {"error": str(e)}
     # 4. batched ansatz: 256 parameter sets x 20 qubits, 12 layers, <H> per set, one graph
     try:
         nb, lb, cnt = 20, 12, 256
@@ -604,6 +694,29 @@ def extras(args, qv, torch, dev, h64, gates):
             qv.qv_destroy(hh)
     except Exception as e:  # noqa: BLE001
         res["batch_ansatz"] = {"error": str(e)}
+    # 5. uneven batch: 64 random circuits, 16..28 qubits, depth 10..60, one persistent
+    # launch per tile size, tile size autotuned per qubit count at creation (last: the
+    # tuning sets the default tile size of those qubit counts for the rest of the process)
+    try:
+        spec = W.uneven_batch(64, W.config_seed(4))
+        circs = [W.random_circuit(n_u, d_u, s_u) for n_u, d_u, s_u in spec]
+        hs_u = [qv.qv_create(n_u, qv.QV_C64) for n_u, _, _ in spec]
+        t0 = time.perf_counter()
+        bu = qv.Batch(list(zip(hs_u, circs)), flags=qv.QV_PLAN_AUTOTUNE)
+        create_s = time.perf_counter() - t0
+        ms_u = _timed(torch, dev, bu.run, 2)
+        upd = sum(len(c) * (1 << n_u) for c, (n_u, _, _) in zip(circs, spec))
+        res["uneven_batch"] = {"workload": "64 random circuits, qubits uniform in [16, 28], depth uniform in [10, 60], "
+                                           "complex64", "ms_per_batch": ms_u, "updates_per_s": upd / (ms_u / 1e3),
+                               "create_s_with_autotune": create_s,
+                               "tile_bits_per_qubits": {str(n_u): qv.qv_default_tile_bits(n_u, qv.QV_C64)
+                                                        for n_u in sorted({x[0] for x in spec})},
+                               "launch_groups": bu.info()}
+        bu.close()
+        for hh in hs_u:
+            qv.qv_destroy(hh)
+    except Exception as e:  # noqa: BLE001
+        res["uneven_batch"] = {"error": str(e)}
     return res
 
 

@@ -89,6 +89,9 @@ typedef enum {
 #define QV_PLAN_NO_PAIRS 4   /* fused mode: no 4x4 operations on two register qubits (the
                                 compiled complex64 kernel merges runs of operations on two
                                 qubits into one 4x4 when that takes fewer FP32 operations) */
+#define QV_PLAN_AUTOTUNE 16  /* qv_batch_create: run the autotuner once for every qubit count of
+                                the batch that has no tuned tile size yet (on the first state of
+                                that size with its circuit; the batch run resets the states) */
 #define QV_PLAN_TENSOR 8     /* fused mode, complex64, tiles of 2^11 or 2^12: every stage of a
                                 pass multiplies its gates into one 16x16 complex matrix and
                                 applies it on the tensor cores (tcgen05, TF32 operands split
@@ -246,12 +249,20 @@ qv_status qv_plan_cost(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv
 int32_t qv_default_tile_bits(int n, qv_dtype dt, int32_t flags);
 
 /* Autotuner: runs g[0..ng) in fused mode with every supported tile size
- * (2^10 .. 2^12 amplitudes, at most 2^n), times each with CUDA events after a
- * warm-up run, and remembers the fastest for this (n, dtype, engine) -- later
- * fused calls, batches and plans with tile_bits = 0 use it. opts selects the
- * engine (QV_PLAN_INTERPRET) and fusion flags; *best_tile_bits gets the
- * winner. Overwrites the state (it is |0...0> on return). Synchronises. */
+ * (2^10 .. 2^12 amplitudes, at most 2^n) and, for the compiled complex64
+ * engine, every schedule variant (FP32 passes with 4x4 pair operations,
+ * without them, and tensor-core stages, whose register sets and transposes
+ * differ), times each with CUDA events after a warm-up run, and remembers the
+ * fastest for this (n, dtype, engine) -- later fused calls, batches and plans
+ * with tile_bits = 0 and no engine flags use it. opts selects the engine
+ * (QV_PLAN_INTERPRET) and fusion flags; *best_tile_bits gets the winning tile
+ * size. Overwrites the state (it is |0...0> on return). Synchronises. */
 qv_status qv_autotune(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t *best_tile_bits);
+
+/* The same; out[0] = the winning tile bits, out[1] = the winning schedule
+ * variant as plan flags (0, QV_PLAN_NO_PAIRS or QV_PLAN_TENSOR). Not in the
+ * paper. */
+qv_status qv_autotune_ex(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t out[2]);
 
 /* Reorders qubits: bit q of every amplitude index moves to bit perm[q]
  * (out[pi(i)] = in[i]). perm is a permutation of 0..n-1. In place. */
@@ -437,6 +448,14 @@ qv_status qv_batch_create(const qv_batch_item *items, size_t count, const qv_pau
  * per state when the batch has a Hamiltonian. QV_ERR_TIMEOUT if a
  * dependency wait in the persistent launch gave up. */
 qv_status qv_batch_run(qv_batch *b, double *expvals);
+
+/* How a batch runs, for inspection (host only): per persistent launch group, 6
+ * values -- tile bits, circuits, qubits of its first circuit, 1 for the
+ * compiled kernel (circuits of one plan structure) or 0 for the interpreting
+ * one, the circuits whose passes of one round are queued together (compiled
+ * kernel; 0 otherwise) and tiles per work item. Writes at most cap groups to
+ * out; returns the number of groups, or -1 for a NULL batch. Not in the paper. */
+int32_t qv_batch_info(const qv_batch *b, int32_t *out, size_t cap);
 
 qv_status qv_batch_destroy(qv_batch *b);
 

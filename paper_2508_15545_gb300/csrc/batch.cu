@@ -243,6 +243,7 @@ struct BatchGroup {
     void *jamps = nullptr, *jcoefs = nullptr;
     uint64_t ntiles = 0;
     uint32_t nchunks = 0;
+
 };
 
 }  // namespace qv
@@ -329,12 +330,31 @@ qv_status build(qv_batch *b, const qv_batch_item *items, size_t count, const qv_
                 const qv_plan_opts *opts)
 {
     const bool fuse = !(opts && (opts->flags & QV_PLAN_NO_FUSION));
+    const bool jit_ok = sizeof(R) == 4 && jit_available(nullptr) && !(opts && (opts->flags & QV_PLAN_INTERPRET));
+    // ---- with QV_PLAN_AUTOTUNE, time the tile sizes once per qubit count not tuned yet
+    // (on the first state of that size, with its circuit; the run resets the states)
+    if (opts && (opts->flags & QV_PLAN_AUTOTUNE) && !opts->tile_bits) {
+        std::map<int, size_t> first;
+        for (size_t c = 0; c < count; ++c) first.emplace(items[c].state->n, c);
+        for (auto &kv : first) {
+            if (kv.first < plan::kMinK || tile_bits_tuned(kv.first, b->dt, !jit_ok)) continue;
+            qv_plan_opts o{};
+            o.flags = jit_ok ? 0 : QV_PLAN_INTERPRET;
+            QV_TRY(autotune(items[kv.second].state, items[kv.second].gates, items[kv.second].ngates, &o, nullptr,
+                            nullptr, false));
+            QV_CUDA(cudaStreamSynchronize(items[kv.second].state->stream));
+        }
+    }
     // ---- plan every circuit, group by tile size
     std::map<int, std::vector<int>> by_k;
     std::vector<std::vector<plan::Pass>> plans(count);
     for (size_t c = 0; c < count; ++c) {
         const int n = items[c].state->n;
-        int K = opts && opts->tile_bits ? opts->tile_bits : tuned_tile_bits(n, b->dt, true);
+        // the tile size the autotuner chose for the engine that will most likely
+        // run it; untuned, 2^12 (the batch kernels hold no next tile in
+        // registers: 256 x 20 qubits took 47 ms at 2^12, 51 ms at 2^11)
+        int K = opts && opts->tile_bits ? opts->tile_bits
+                : tile_bits_tuned(n, b->dt, !jit_ok) ? tuned_tile_bits(n, b->dt, !jit_ok) : std::min(n, plan::kMaxK);
         if (K > n) K = n;
         if (K < plan::kMinK || K > plan::kMaxK)
             return fail(QV_ERR_UNSUPPORTED, "batch item %zu: %d qubits is below the smallest tile (%d)", c, n,
@@ -365,7 +385,6 @@ qv_status build(qv_batch *b, const qv_batch_item *items, size_t count, const qv_
     QV_TRY(dmalloc(b, &st, sizeof(int)));
     b->status = static_cast<int *>(st);
     // ---- one persistent launch per tile size
-    const bool jit_ok = sizeof(R) == 4 && jit_available(nullptr) && !(opts && (opts->flags & QV_PLAN_INTERPRET));
     for (auto &kv : by_k) {
         BatchGroup g;
         g.K = kv.first;
@@ -592,6 +611,21 @@ qv_status batch_create(const qv_batch_item *items, size_t count, const qv_pauli_
     }
     *out = b;
     return QV_OK;
+}
+
+size_t batch_info(const qv_batch *b, int32_t *out, size_t cap)
+{
+    for (size_t g = 0; g < b->groups.size() && g < cap; ++g) {
+        const BatchGroup &G = b->groups[g];
+        int32_t *o = out + 6 * g;
+        o[0] = G.K;
+        o[1] = int32_t(G.circuits.size());
+        o[2] = b->states[size_t(G.circuits.front())]->n;
+        o[3] = G.jit ? 1 : 0;
+        o[4] = int32_t(G.jit ? G.circuits.size() : 0);  // one round of every circuit at a time
+        o[5] = int32_t(kChunkTiles);
+    }
+    return b->groups.size();
 }
 
 qv_status batch_run(qv_batch *b, double *expvals)

@@ -291,7 +291,11 @@ qv_status apply_fused(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_op
     int K = (opts && opts->tile_bits) ? opts->tile_bits : default_tile_bits(s, opts);
     if (K < plan::kMinK || K > plan::kMaxK) return fail(QV_ERR_ARG, "tile_bits %d outside [10, 12]", K);
     if (K > s->n) return fail(QV_ERR_ARG, "tile_bits %d exceeds n = %d", K, s->n);
-    const int flags = opts ? opts->flags : 0;
+    int flags = opts ? opts->flags : 0;
+    // the autotuner's schedule variant goes with its tile size
+    if (!(opts && opts->tile_bits) && !s->host_mem &&
+        !(flags & (QV_PLAN_NO_FUSION | QV_PLAN_INTERPRET | QV_PLAN_NO_PAIRS | QV_PLAN_TENSOR)))
+        flags |= tuned_flags(s->n, s->dt, !jit_available(nullptr));
     const bool fuse = !(flags & QV_PLAN_NO_FUSION);
     const bool jit = !(flags & QV_PLAN_INTERPRET) && jit_available(nullptr);
     const bool tc = (flags & QV_PLAN_TENSOR) != 0;

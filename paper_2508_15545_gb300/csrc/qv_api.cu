@@ -528,7 +528,23 @@ qv_status qv_autotune(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_op
     CHECK_HANDLE(s);
     if (ng && !g) return fail(QV_ERR_ARG, "gate list is NULL");
     for (size_t k = 0; k < ng; ++k) QV_TRY(validate_gate(g[k], s->n, k));
-    return autotune(s, g, ng, opts, best_tile_bits);
+    return autotune(s, g, ng, opts, best_tile_bits, nullptr);
+}
+
+qv_status qv_autotune_ex(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t out[2])
+{
+    CHECK_HANDLE(s);
+    if (!out) return fail(QV_ERR_ARG, "out is NULL");
+    if (ng && !g) return fail(QV_ERR_ARG, "gate list is NULL");
+    for (size_t k = 0; k < ng; ++k) QV_TRY(validate_gate(g[k], s->n, k));
+    return autotune(s, g, ng, opts, out, out + 1);
+}
+
+int32_t qv_batch_info(const qv_batch *b, int32_t *out, size_t cap)
+{
+    if (!b) return -1;
+    if (cap && !out) return -1;
+    return int32_t(batch_info(b, out, cap));
 }
 
 qv_status qv_batch_create(const qv_batch_item *items, size_t count, const qv_pauli_term *H, size_t nt,

@@ -38,12 +38,23 @@ qv_status to_pgates(const qv_gate *g, size_t ng, std::vector<plan::PGate> &out);
 // Tile bits to use by default: the autotuned value for (n, dtype, engine) when
 // one was measured, else min(n, 12).
 int tuned_tile_bits(int n, qv_dtype dt, bool interpreting = true);
-qv_status autotune(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t *best_out);
+// Engine flags (QV_PLAN_NO_PAIRS, QV_PLAN_TENSOR) the autotuner chose with that
+// tile size, 0 when untuned; whether (n, dtype, engine) was tuned at all.
+int tuned_flags(int n, qv_dtype dt, bool interpreting);
+bool tile_bits_tuned(int n, qv_dtype dt, bool interpreting);
+// Times the fused path with every tile size (and, with `variants`, the
+// schedule variants: 4x4 pair operations on or off, tensor-core stages) on the
+// caller's circuit and keeps the fastest for (n, dtype, engine).
+qv_status autotune(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t *best_k,
+                   int32_t *best_flags, bool variants = true);
 
 // ---- batched circuits (batch.cu)
 qv_status batch_create(const qv_batch_item *items, size_t count, const qv_pauli_term *H, size_t nt,
                        const qv_plan_opts *opts, qv_batch **out);
 qv_status batch_run(qv_batch *b, double *expvals);
+// Per launch group: tile bits, circuits, qubits of its first circuit, compiled
+// (1) or interpreting (0), L2 group size and tiles per work item (6 values each).
+size_t batch_info(const qv_batch *b, int32_t *out, size_t cap);
 // Launches one bounded wait on a counter nothing increments (`limit` polls).
 qv_status wait_selftest(qv_state *s, uint32_t limit);
 void batch_release(qv_batch *b);

@@ -22,6 +22,7 @@ QV_PLAN_NO_FUSION = 1
 QV_PLAN_INTERPRET = 2
 QV_PLAN_NO_PAIRS = 4
 QV_PLAN_TENSOR = 8
+QV_PLAN_AUTOTUNE = 16
 QV_ALLOC_HOST = 1
 QV_SWEEP_AUTO, QV_SWEEP_PER_GATE, QV_SWEEP_TILES, QV_SWEEP_COMPILED = 0, 1, 2, 3
 STATUS_NAMES = {0: "QV_OK", 1: "QV_ERR_ARG", 2: "QV_ERR_OOM", 3: "QV_ERR_CUDA",
@@ -119,6 +120,8 @@ def _load():
                             ctypes.c_size_t, ctypes.c_size_t, P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32],
         "qv_autotune": [_H, ctypes.POINTER(qv_gate), ctypes.c_size_t, ctypes.POINTER(qv_plan_opts),
                         ctypes.POINTER(ctypes.c_int32)],
+        "qv_autotune_ex": [_H, ctypes.POINTER(qv_gate), ctypes.c_size_t, ctypes.POINTER(qv_plan_opts),
+                           ctypes.POINTER(ctypes.c_int32)],
         "qv_batch_create": [ctypes.POINTER(qv_batch_item), ctypes.c_size_t, ctypes.POINTER(qv_pauli_term),
                             ctypes.c_size_t, ctypes.POINTER(qv_plan_opts), ctypes.POINTER(ctypes.c_void_p)],
         "qv_batch_run": [ctypes.c_void_p, P],
@@ -140,6 +143,8 @@ def _load():
         f = getattr(L, name)
         f.argtypes = args
         f.restype = st
+    L.qv_batch_info.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
+    L.qv_batch_info.restype = ctypes.c_int32
     L.qv_last_error.argtypes = []
     L.qv_last_error.restype = ctypes.c_char_p
     return L
@@ -422,6 +427,26 @@ def qv_autotune(h: int, gates, flags: int = 0) -> int:
     return best.value
 
 
+def qv_autotune_ex(h: int, gates, flags: int = 0):
+    """Like qv_autotune, also over the schedule variants; returns (tile bits, plan flags)."""
+    arr, ng = _gate_array(gates)
+    opts = plan_opts(QV_MODE_FUSED, 0, flags)
+    out = (ctypes.c_int32 * 2)()
+    _check(lib.qv_autotune_ex(h, arr, ng, ctypes.byref(opts), out))
+    return int(out[0]), int(out[1])
+
+
+def qv_batch_info(b) -> list:
+    """Per launch group of a batch: dict of tile_bits, circuits, qubits, compiled, l2_group, chunk_tiles."""
+    n = lib.qv_batch_info(b, None, 0)
+    if n < 0:
+        raise QvError(QV_ERR_ARG, "bad batch")
+    out = (ctypes.c_int32 * max(1, 6 * n))()
+    lib.qv_batch_info(b, out, n)
+    keys = ("tile_bits", "circuits", "qubits", "compiled", "l2_group", "chunk_tiles")
+    return [dict(zip(keys, [int(out[6 * g + i]) for i in range(6)])) for g in range(n)]
+
+
 def qv_apply_batch(items, terms=None, tile_bits: int = 0, flags: int = 0) -> np.ndarray:
     """One-shot batch (qv_apply_batch): runs every (state, circuit) pair from
     |0...0> and returns <H> per state (zeros without terms)."""
@@ -464,6 +489,9 @@ class Batch:
         out = np.zeros(self.count)
         _check(lib.qv_batch_run(self.b, out.ctypes.data if self.has_h else None))
         return out
+
+    def info(self) -> list:
+        return qv_batch_info(self.b)
 
     def close(self):
         if self.b:

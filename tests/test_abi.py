@@ -38,6 +38,8 @@ def test_struct_layouts_match_header(qvlib):
     assert ctypes.sizeof(qvlib.qv_gate) == 120
     assert ctypes.sizeof(qvlib.qv_plan_opts) == 32
     assert ctypes.sizeof(qvlib.qv_pauli_term) == 24
+    # qv_tc_stage: 40 int32 + 2 * 256 complex128
+    assert ctypes.sizeof(qvlib.qv_tc_stage) == 160 + 2 * 256 * 16
     assert ctypes.sizeof(qvlib.qv_kernel_stat) == 24
 
 

@@ -113,3 +113,71 @@ def test_bounded_wait_reports_timeout(qvlib, orc, cuda):
     psi = qv.qv_get_state(h)
     assert np.linalg.norm(psi.astype(complex) - orc.run(n, gates)) <= 1e-5
     qv.qv_destroy(h)
+
+
+def test_batch_compiled_many_sets(qvlib, orc, cuda):
+    """Forty parameter sets of one ansatz (one plan structure, the compiled
+    kernel): energies equal the oracle's on sampled sets and the one-by-one GPU
+    path on all of them; the batch reports its launch group."""
+    qv = qvlib
+    n, layers, count = 18, 6, 40
+    terms = W.ansatz_hamiltonian(n)
+    circuits = [W.ansatz_circuit(n, layers, W.config_seed(2, 300 + c))[0] for c in range(count)]
+    states = [qv.qv_create(n, 0) for _ in range(count)]
+    try:
+        b = qv.Batch(list(zip(states, circuits)), terms)
+        info = b.info()
+        assert len(info) == 1 and info[0]["compiled"] == 1 and info[0]["circuits"] == count
+        assert info[0]["qubits"] == n and info[0]["chunk_tiles"] == 32
+        e = b.run()
+        for c in (0, 23, count - 1):
+            assert e[c] == pytest.approx(orc.energy(n, circuits[c], terms), abs=2e-5), c
+        h = qv.qv_create(n, 0)
+        for c in range(count):
+            qv.qv_set_basis(h, 0)
+            qv.qv_apply_circuit(h, circuits[c])
+            assert e[c] == pytest.approx(qv.qv_expect_pauli(h, terms), abs=2e-5), c
+        qv.qv_destroy(h)
+        b.close()
+    finally:
+        for h in states:
+            qv.qv_destroy(h)
+
+
+def test_batch_autotunes_each_qubit_count(qvlib, orc, cuda):
+    """QV_PLAN_AUTOTUNE at batch creation tunes every qubit count once; the
+    batch then runs with the tuned tile sizes and gives the oracle's states."""
+    qv = qvlib
+    spec = [(13, 6), (15, 5), (13, 4), (16, 3)]
+    circuits = [W.random_circuit(n, d, seed=1300 + k) for k, (n, d) in enumerate(spec)]
+    states = [qv.qv_create(n, 0) for n, _ in spec]
+    try:
+        b = qv.Batch(list(zip(states, circuits)), flags=qv.QV_PLAN_AUTOTUNE)
+        for g in b.info():
+            assert g["tile_bits"] == qv.qv_default_tile_bits(g["qubits"], 0)
+        b.run()
+        for (n, _), h, g in zip(spec, states, circuits):
+            assert np.linalg.norm(qv.qv_get_state(h).astype(complex) - orc.run(n, g)) <= 1e-5, n
+        b.close()
+    finally:
+        for h in states:
+            qv.qv_destroy(h)
+
+
+def test_autotune_schedule_variants(qvlib, orc, cuda):
+    """The autotuner over tile sizes and schedule variants (pair operations on
+    or off, tensor-core stages): it reports one of them, and the next fused call
+    with no tile size or engine flags uses it and gives the oracle's state."""
+    qv = qvlib
+    n = 17
+    g = W.random_circuit(n, 8, seed=17)
+    h = qv.qv_create(n, 0)
+    try:
+        k, fl = qv.qv_autotune_ex(h, g)
+        assert k in (10, 11, 12) and fl in (0, qv.QV_PLAN_NO_PAIRS, qv.QV_PLAN_TENSOR)
+        assert not (fl == qv.QV_PLAN_TENSOR and k < 11)
+        assert qv.qv_default_tile_bits(n, 0) == k
+        qv.qv_apply_circuit(h, g, mode=qv.QV_MODE_FUSED)
+        assert np.linalg.norm(qv.qv_get_state(h).astype(complex) - orc.run(n, g)) <= 1e-5
+    finally:
+        qv.qv_destroy(h)
