@@ -482,6 +482,46 @@ qv_status qv_wait_selftest(qv_state *s, uint32_t limit);
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *qv_last_error(void);
 
+/* ------------------------------------------------------------------------ */
+/* A state split over 2^g ranks (Sec. III-D, Eq. 9): schedule, host only.     */
+/* ------------------------------------------------------------------------ */
+
+/* Rank r of C = 2^g holds amplitudes [r 2^n / C, (r + 1) 2^n / C - 1] (Eq. 9):
+ * the top g physical qubits name the rank ("global"), the low L = n - g the
+ * position in its shard ("local"). qv_dist_plan turns a circuit into this
+ * rank's steps:
+ *   QV_DIST_LOCAL     run local_gates[gate_begin, gate_end) on the shard (an
+ *                     L-qubit state; qubit indices are local physical ones);
+ *   QV_DIST_EXCHANGE  trade one half of the shard with rank `peer` = rank XOR
+ *                     2^global_bit: the upper half (local bit L - 1 = 1) when
+ *                     send_upper, else the lower half; the partner's half
+ *                     replaces it at the same offsets.
+ * An exchange swaps the global qubit with local qubit L - 1 (Sec. III-D,
+ * Fig. 4: pairs (i, i XOR 2^t) that cross ranks become local). Controls and
+ * diagonal gates on global qubits need no exchange (each rank knows its own
+ * bits) and SWAP gates only relabel qubits, so final_perm[q] (n entries) is
+ * the physical qubit holding logical qubit q at the end. */
+typedef enum { QV_DIST_LOCAL = 0, QV_DIST_EXCHANGE = 1 } qv_dist_kind;
+typedef struct {
+    int32_t  kind;        /* qv_dist_kind */
+    int32_t  global_bit;  /* exchange: j, the rank bit of the global qubit */
+    int32_t  peer;        /* exchange: rank XOR 2^j */
+    int32_t  send_upper;  /* exchange: 1 = the half with local bit L - 1 = 1 */
+    uint64_t gate_begin;  /* local: first gate of the step in local_gates */
+    uint64_t gate_end;    /* local: one past the last */
+} qv_dist_step;
+
+/* Schedule of g[0..ng) on rank `rank` of 2^global_bits ranks (1 <= global_bits
+ * < n, 0 <= rank < 2^global_bits). With steps or local_gates NULL only the
+ * counts *nsteps and *ngates are written; otherwise steps_cap and gates_cap
+ * must hold them (QV_ERR_ARG if not). final_perm (n int32) may be NULL. Every
+ * rank calls it with the same gates and gets the same sequence of step kinds
+ * and exchange partners in matching order. Not in the paper beyond Eq. 9 and
+ * Fig. 4: the exchange rule is this library's reading of Sec. III-D. */
+qv_status qv_dist_plan(int n, int global_bits, int rank, const qv_gate *g, size_t ng, qv_dist_step *steps,
+                       size_t steps_cap, size_t *nsteps, qv_gate *local_gates, size_t gates_cap, size_t *ngates,
+                       int32_t *final_perm);
+
 #ifdef __cplusplus
 }
 #endif

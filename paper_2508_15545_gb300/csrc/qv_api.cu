@@ -413,6 +413,30 @@ qv_status qv_plan_source(int n, qv_dtype dt, const qv_gate *g, size_t ng, const 
     return QV_OK;
 }
 
+qv_status qv_dist_plan(int n, int global_bits, int rank, const qv_gate *g, size_t ng, qv_dist_step *steps,
+                       size_t steps_cap, size_t *nsteps, qv_gate *local_gates, size_t gates_cap, size_t *ngates,
+                       int32_t *final_perm)
+{
+    if (!nsteps || !ngates) return fail(QV_ERR_ARG, "nsteps or ngates is NULL");
+    QV_TRY(check_plan_args(n, QV_C64, g, ng));
+    if (global_bits < 1 || global_bits >= n || global_bits > 30)
+        return fail(QV_ERR_ARG, "global_bits = %d outside [1, n - 1]", global_bits);
+    if (rank < 0 || rank >= (1 << global_bits)) return fail(QV_ERR_ARG, "rank %d outside [0, 2^%d)", rank, global_bits);
+    std::vector<qv_dist_step> st;
+    std::vector<qv_gate> lg;
+    std::vector<int32_t> perm;
+    QV_TRY(dist_plan(n, global_bits, rank, g, ng, st, lg, perm));
+    *nsteps = st.size();
+    *ngates = lg.size();
+    if (final_perm) std::copy(perm.begin(), perm.end(), final_perm);
+    if (!steps || !local_gates) return QV_OK;
+    if (steps_cap < st.size() || gates_cap < lg.size())
+        return fail(QV_ERR_ARG, "buffers too small: %zu steps and %zu gates needed", st.size(), lg.size());
+    std::copy(st.begin(), st.end(), steps);
+    std::copy(lg.begin(), lg.end(), local_gates);
+    return QV_OK;
+}
+
 qv_status qv_plan_tc_stage(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int32_t pass,
                            int32_t stage, qv_tc_stage *out)
 {

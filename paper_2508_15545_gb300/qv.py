@@ -59,6 +59,14 @@ class qv_tc_stage(ctypes.Structure):
                 ("has_matrix", ctypes.c_int32), ("ext", ctypes.c_int32), ("m", (qv_c128 * 256) * 2)]
 
 
+class qv_dist_step(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("global_bit", ctypes.c_int32), ("peer", ctypes.c_int32),
+                ("send_upper", ctypes.c_int32), ("gate_begin", ctypes.c_uint64), ("gate_end", ctypes.c_uint64)]
+
+
+QV_DIST_LOCAL, QV_DIST_EXCHANGE = 0, 1
+
+
 class qv_kernel_stat(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint64), ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
 
@@ -107,6 +115,10 @@ def _load():
                            ctypes.POINTER(ctypes.c_size_t)],
         "qv_plan_compile": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(qv_gate), ctypes.c_size_t,
                             ctypes.POINTER(qv_plan_opts), ctypes.POINTER(ctypes.c_int64)],
+        "qv_dist_plan": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(qv_gate), ctypes.c_size_t,
+                         ctypes.POINTER(qv_dist_step), ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t),
+                         ctypes.POINTER(qv_gate), ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t),
+                         ctypes.POINTER(ctypes.c_int32)],
         "qv_plan_tc_stage": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(qv_gate), ctypes.c_size_t,
                              ctypes.POINTER(qv_plan_opts), ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(qv_tc_stage)],
         "qv_norm2": [_H, ctypes.POINTER(ctypes.c_double)],
@@ -358,6 +370,33 @@ def qv_plan_tc_stage(n: int, gates, pass_index: int, stage: int, tile_bits: int 
             "in_reg": list(o.in_reg), "in_thr": list(o.in_thr)[:k - 4],
             "out_reg": list(o.out_reg), "out_thr": list(o.out_thr)[:k - 4],
             "has_matrix": bool(o.has_matrix), "ext": int(o.ext), "m": m}
+
+
+def qv_dist_plan(n: int, global_bits: int, rank: int, gates):
+    """Schedule of ``gates`` on ``rank`` of 2^global_bits ranks (Eq. 9; host
+    only): (steps, local gate array, final_perm). steps: list of dicts with
+    kind 'local' (begin, end into the local gate array) or 'exchange' (peer,
+    global_bit, send_upper)."""
+    if isinstance(gates, tuple) and len(gates) == 2 and isinstance(gates[1], int):
+        arr, ng = gates
+    else:
+        arr, ng = gates_to_c(gates), len(gates)
+    ns, nl = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib.qv_dist_plan(n, global_bits, rank, arr, ng, None, 0, ctypes.byref(ns), None, 0, ctypes.byref(nl), None))
+    st = (qv_dist_step * max(1, ns.value))()
+    lg = (qv_gate * max(1, nl.value))()
+    perm = (ctypes.c_int32 * n)()
+    _check(lib.qv_dist_plan(n, global_bits, rank, arr, ng, st, ns.value, ctypes.byref(ns), lg, nl.value,
+                            ctypes.byref(nl), perm))
+    steps = []
+    for k in range(ns.value):
+        x = st[k]
+        if x.kind == QV_DIST_LOCAL:
+            steps.append({"kind": "local", "begin": int(x.gate_begin), "end": int(x.gate_end)})
+        else:
+            steps.append({"kind": "exchange", "peer": int(x.peer), "global_bit": int(x.global_bit),
+                          "send_upper": bool(x.send_upper)})
+    return steps, (lg, nl.value), list(perm)
 
 
 def qv_permute_qubits(h: int, perm: Sequence[int]):
