@@ -375,10 +375,13 @@ qv_status qv_distance(qv_state *a, qv_state *b, double *out);
  * present on every device that loads it until the process exits. The first
  * call on a device looks that array's address up (cudaGetSymbolAddress, which
  * may load the library's device code); make that first call before any stream
- * capture. Every call shares the array, so calls that can overlap on the GPU
- * (different streams without ordering) race and give wrong sums; calls on one
- * stream are safe. Nothing in the array needs to start at zero: every call
- * overwrites the part it reads. */
+ * capture. The address is kept for the life of the process: after a
+ * cudaDeviceReset of that device it is stale, so do not call this entry point
+ * on a device that was reset. dev_amp, dev_out and the stream must belong to
+ * the current device (QV_ERR_ARG otherwise). Every call shares the array, so
+ * calls that can overlap on the GPU (different streams without ordering) race
+ * and give wrong sums; calls on one stream are safe. Nothing in the array needs
+ * to start at zero: every call overwrites the part it reads. */
 qv_status qv_zsums_noalloc(const void *dev_amp, int n, qv_dtype dt, void *cuda_stream, double *dev_out);
 
 /* ------------------------------------------------------------------------ */
@@ -451,9 +454,11 @@ qv_status qv_batch_run(qv_batch *b, double *expvals);
 
 /* How a batch runs, for inspection (host only): per persistent launch group, 6
  * values -- tile bits, circuits, qubits of its first circuit, 1 for the
- * compiled kernel (circuits of one plan structure) or 0 for the interpreting
- * one, the circuits whose passes of one round are queued together (compiled
- * kernel; 0 otherwise) and tiles per work item. Writes at most cap groups to
+ * compiled kernel (circuits of one plan structure), 0 for the interpreting
+ * one, 2 for a circuit large enough to fill the GPU alone (at least 2^12
+ * tiles per pass: its own compiled fused passes, in the same graph), then the
+ * circuits whose passes of one round are queued together (compiled kernel; 0
+ * otherwise) and tiles per work item (0 for a circuit of its own). Writes at most cap groups to
  * out; returns the number of groups, or -1 for a NULL batch. Not in the paper. */
 int32_t qv_batch_info(const qv_batch *b, int32_t *out, size_t cap);
 
@@ -511,6 +516,10 @@ typedef struct {
     uint64_t gate_end;    /* local: one past the last */
 } qv_dist_step;
 
+/* qv_dist_plan flags: QV_DIST_RESTORE appends the steps that bring every
+ * logical qubit back to its own physical position (final_perm = identity). */
+#define QV_DIST_RESTORE 1
+
 /* Schedule of g[0..ng) on rank `rank` of 2^global_bits ranks (1 <= global_bits
  * < n, 0 <= rank < 2^global_bits). With steps or local_gates NULL only the
  * counts *nsteps and *ngates are written; otherwise steps_cap and gates_cap
@@ -518,9 +527,9 @@ typedef struct {
  * rank calls it with the same gates and gets the same sequence of step kinds
  * and exchange partners in matching order. Not in the paper beyond Eq. 9 and
  * Fig. 4: the exchange rule is this library's reading of Sec. III-D. */
-qv_status qv_dist_plan(int n, int global_bits, int rank, const qv_gate *g, size_t ng, qv_dist_step *steps,
-                       size_t steps_cap, size_t *nsteps, qv_gate *local_gates, size_t gates_cap, size_t *ngates,
-                       int32_t *final_perm);
+qv_status qv_dist_plan(int n, int global_bits, int rank, const qv_gate *g, size_t ng, int32_t flags,
+                       qv_dist_step *steps, size_t steps_cap, size_t *nsteps, qv_gate *local_gates, size_t gates_cap,
+                       size_t *ngates, int32_t *final_perm);
 
 #ifdef __cplusplus
 }

@@ -12,6 +12,7 @@
 // on timeout the kernel writes QV_ERR_TIMEOUT to a status word and returns.
 #include <algorithm>
 #include <map>
+#include <memory>
 #include <vector>
 
 #include "fused_device.cuh"
@@ -265,6 +266,12 @@ struct qv_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<void *> owned;
+    // circuits that fill the GPU alone: their own compiled fused passes, in the same graph
+    struct Solo {
+        int circuit = 0, K = 0;
+        std::shared_ptr<qv::JitProgram> prog;
+    };
+    std::vector<Solo> solo;
 };
 
 namespace qv {
@@ -331,15 +338,48 @@ qv_status build(qv_batch *b, const qv_batch_item *items, size_t count, const qv_
 {
     const bool fuse = !(opts && (opts->flags & QV_PLAN_NO_FUSION));
     const bool jit_ok = sizeof(R) == 4 && jit_available(nullptr) && !(opts && (opts->flags & QV_PLAN_INTERPRET));
-    // ---- with QV_PLAN_AUTOTUNE, time the tile sizes once per qubit count not tuned yet
-    // (on the first state of that size, with its circuit; the run resets the states)
-    if (opts && (opts->flags & QV_PLAN_AUTOTUNE) && !opts->tile_bits) {
+    const bool fixed_k = opts && opts->tile_bits;
+    // ---- circuits whose every pass fills the GPU (at least 2^12 tiles) run on
+    // their own compiled passes, as qv_apply_circuit would run them; the
+    // persistent queue takes the rest
+    std::vector<char> solo(count, 0);
+    auto solo_k = [&](int n) { return fixed_k ? opts->tile_bits : tuned_tile_bits(n, b->dt, false); };
+    if (jit_ok)
+        for (size_t c = 0; c < count; ++c) solo[c] = items[c].state->n - solo_k(items[c].state->n) >= 12;
+    // qubit counts whose queued circuits all share one gate structure run in the
+    // compiled persistent kernel, the others in the interpreting one
+    std::map<int, bool> uniform;
+    {
+        std::map<int, size_t> first;
+        for (size_t c = 0; c < count; ++c) {
+            if (solo[c]) continue;
+            const int n = items[c].state->n;
+            auto it = first.find(n);
+            if (it == first.end()) {
+                first[n] = c;
+                uniform[n] = jit_ok;
+                continue;
+            }
+            const qv_batch_item &a = items[it->second], &x = items[c];
+            bool same = a.ngates == x.ngates;
+            for (size_t k = 0; same && k < x.ngates; ++k)
+                same = a.gates[k].kind == x.gates[k].kind && a.gates[k].target == x.gates[k].target &&
+                       a.gates[k].target2 == x.gates[k].target2 && a.gates[k].ctrl == x.gates[k].ctrl;
+            uniform[n] = uniform[n] && same;
+        }
+    }
+    auto engine_interp = [&](size_t c) { return !solo[c] && !uniform[items[c].state->n]; };
+    // ---- with QV_PLAN_AUTOTUNE, time the tile sizes once per qubit count not tuned yet,
+    // with the engine that will run it (on the first state of that size, with its
+    // circuit; the run resets the states)
+    if (opts && (opts->flags & QV_PLAN_AUTOTUNE) && !fixed_k) {
         std::map<int, size_t> first;
         for (size_t c = 0; c < count; ++c) first.emplace(items[c].state->n, c);
         for (auto &kv : first) {
-            if (kv.first < plan::kMinK || tile_bits_tuned(kv.first, b->dt, !jit_ok)) continue;
+            const bool interp = engine_interp(kv.second) || !jit_ok;
+            if (kv.first < plan::kMinK || tile_bits_tuned(kv.first, b->dt, interp)) continue;
             qv_plan_opts o{};
-            o.flags = jit_ok ? 0 : QV_PLAN_INTERPRET;
+            o.flags = interp ? QV_PLAN_INTERPRET : 0;
             QV_TRY(autotune(items[kv.second].state, items[kv.second].gates, items[kv.second].ngates, &o, nullptr,
                             nullptr, false));
             QV_CUDA(cudaStreamSynchronize(items[kv.second].state->stream));
@@ -350,11 +390,27 @@ qv_status build(qv_batch *b, const qv_batch_item *items, size_t count, const qv_
     std::vector<std::vector<plan::Pass>> plans(count);
     for (size_t c = 0; c < count; ++c) {
         const int n = items[c].state->n;
-        // the tile size the autotuner chose for the engine that will most likely
-        // run it; untuned, 2^12 (the batch kernels hold no next tile in
-        // registers: 256 x 20 qubits took 47 ms at 2^12, 51 ms at 2^11)
-        int K = opts && opts->tile_bits ? opts->tile_bits
-                : tile_bits_tuned(n, b->dt, !jit_ok) ? tuned_tile_bits(n, b->dt, !jit_ok) : std::min(n, plan::kMaxK);
+        if (solo[c]) {
+            const int K = std::min(n, solo_k(n));
+            std::vector<plan::PGate> pg;
+            QV_TRY(to_pgates(items[c].gates, items[c].ngates, pg));
+            plan::PlanStats st;
+            std::string err;
+            if (!plan::make_plan(n, K, true, fuse, fuse, pg, plans[c], st, err))
+                return fail(QV_ERR_UNSUPPORTED, "batch item %zu: planner: %s", c, err.c_str());
+            qv_batch::Solo so;
+            so.circuit = int(c);
+            so.K = K;
+            QV_TRY(jit_prepare(items[c].state, plans[c], so.prog));
+            b->solo.push_back(std::move(so));
+            continue;
+        }
+        // the tile size the autotuner chose for the engine that will run it;
+        // untuned, 2^12 (the batch kernels hold no next tile in registers: 256 x
+        // 20 qubits took 47 ms at 2^12, 51 ms at 2^11)
+        const bool interp = engine_interp(c) || !jit_ok;
+        int K = fixed_k ? opts->tile_bits
+                : tile_bits_tuned(n, b->dt, interp) ? tuned_tile_bits(n, b->dt, interp) : std::min(n, plan::kMaxK);
         if (K > n) K = n;
         if (K < plan::kMinK || K > plan::kMaxK)
             return fail(QV_ERR_UNSUPPORTED, "batch item %zu: %d qubits is below the smallest tile (%d)", c, n,
@@ -544,6 +600,11 @@ qv_status build(qv_batch *b, const qv_batch_item *items, size_t count, const qv_
             const bool ok = launch_group<R>(b, b->groups[gi], b->next + gi);
             ce = ok ? cudaGetLastError() : cudaErrorLaunchFailure;
         }
+        for (const auto &so : b->solo) {
+            if (ce != cudaSuccess) break;
+            const qv_status r = jit_launch(items[so.circuit].state, *so.prog, b->stream);
+            ce = r == QV_OK ? cudaGetLastError() : cudaErrorLaunchFailure;
+        }
         if (nt && ce == cudaSuccess) {
             batch_pauli_kernel<R><<<dim3(kBlocksPerState, unsigned(count)), kBThreads,
                                     b->nhgroups * sizeof(BGroup), b->stream>>>(
@@ -625,7 +686,20 @@ size_t batch_info(const qv_batch *b, int32_t *out, size_t cap)
         o[4] = int32_t(G.jit ? G.circuits.size() : 0);  // one round of every circuit at a time
         o[5] = int32_t(kChunkTiles);
     }
-    return b->groups.size();
+    size_t g = b->groups.size();
+    for (const auto &so : b->solo) {
+        if (g < cap) {
+            int32_t *o = out + 6 * g;
+            o[0] = so.K;
+            o[1] = 1;
+            o[2] = b->states[size_t(so.circuit)]->n;
+            o[3] = 2;  // its own compiled passes
+            o[4] = 0;
+            o[5] = 0;
+        }
+        ++g;
+    }
+    return g;
 }
 
 qv_status batch_run(qv_batch *b, double *expvals)

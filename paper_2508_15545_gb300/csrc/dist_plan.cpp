@@ -34,7 +34,7 @@
 namespace qv {
 
 qv_status dist_plan(int n, int g, int rank, const qv_gate *gates, size_t ng, std::vector<qv_dist_step> &steps,
-                    std::vector<qv_gate> &lg, std::vector<int32_t> &final_perm)
+                    std::vector<qv_gate> &lg, std::vector<int32_t> &final_perm, bool restore)
 {
     const int L = n - g;
     std::vector<int> perm(n), inv(n);  // logical -> physical, physical -> logical
@@ -73,6 +73,26 @@ qv_status dist_plan(int n, int g, int rank, const qv_gate *gates, size_t ng, std
         inv[pb] = qa;
     };
     auto bit_of_rank = [&](int p) { return (rank >> (p - L)) & 1; };
+    auto local_swap = [&](int pa, int pb) {  // data moves: labels follow
+        qv_gate s{};
+        s.kind = QV_G_SWAP;
+        s.target = pa;
+        s.target2 = pb;
+        s.ctrl = -1;
+        s.param[0] = s.param[1] = s.param[2] = -1;
+        lg.push_back(s);
+        swap_labels(pa, pb);
+    };
+    auto exchange = [&](int pg) {  // global position pg <-> local position L - 1
+        flush();
+        qv_dist_step e{};
+        e.kind = QV_DIST_EXCHANGE;
+        e.global_bit = pg - L;
+        e.peer = rank ^ (1 << (pg - L));
+        e.send_upper = bit_of_rank(pg) == 0 ? 1 : 0;
+        steps.push_back(e);
+        swap_labels(pg, L - 1);
+    };
     for (size_t k = 0; k < ng; ++k) {
         const qv_gate &x = gates[k];
         if (x.kind == QV_G_SWAP) {  // exchange the two logical labels; no data moves
@@ -95,24 +115,8 @@ qv_status dist_plan(int n, int g, int rank, const qv_gate *gates, size_t ng, std
                 }
             }
             if (victim < 0) return fail(QV_ERR_UNSUPPORTED, "no local qubit to exchange (n = %d, g = %d)", n, g);
-            if (victim != L - 1) {
-                qv_gate s{};
-                s.kind = QV_G_SWAP;
-                s.target = victim;
-                s.target2 = L - 1;
-                s.ctrl = -1;
-                s.param[0] = s.param[1] = s.param[2] = -1;
-                lg.push_back(s);
-                swap_labels(victim, L - 1);  // data moved by the local SWAP: labels follow it
-            }
-            flush();
-            qv_dist_step e{};
-            e.kind = QV_DIST_EXCHANGE;
-            e.global_bit = pg - L;
-            e.peer = rank ^ (1 << (pg - L));
-            e.send_upper = bit_of_rank(pg) == 0 ? 1 : 0;
-            steps.push_back(e);
-            swap_labels(pg, L - 1);
+            if (victim != L - 1) local_swap(victim, L - 1);
+            exchange(pg);
         }
         // the gate on this rank
         qv_gate y = x;
@@ -145,6 +149,19 @@ qv_status dist_plan(int n, int g, int rank, const qv_gate *gates, size_t ng, std
         y.target = pt;
         y.ctrl = pc;
         lg.push_back(y);
+    }
+    if (restore) {
+        // back to the natural order: every global position gets its own logical
+        // qubit through local position L - 1, then one local permutation (SWAPs,
+        // relabels in the fused passes) orders the local positions
+        for (int pg = n - 1; pg >= L; --pg) {
+            if (inv[pg] == pg) continue;
+            if (perm[pg] >= L) exchange(perm[pg]);  // logical pg sits at another global position
+            if (perm[pg] != L - 1) local_swap(perm[pg], L - 1);
+            exchange(pg);
+        }
+        for (int p = 0; p < L; ++p)
+            if (inv[p] != p) local_swap(perm[p], p);
     }
     flush();
     final_perm.assign(perm.begin(), perm.end());

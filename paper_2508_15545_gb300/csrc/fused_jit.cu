@@ -27,6 +27,7 @@
 
 #include "coef.h"
 #include "planner.h"
+#include "ptxas_report.h"
 #include "qv_internal.h"
 #include "qv_jit.h"
 
@@ -1318,6 +1319,9 @@ bool compile_one(const std::string &src, std::vector<char> &cubin, std::string &
     return true;
 }
 
+// Threads that compile passes in parallel: at most 16.
+unsigned compile_threads() { return std::max(1u, std::min(16u, std::thread::hardware_concurrency())); }
+
 qv_status cu_fail(CUresult r, const char *what)
 {
     const char *s = nullptr;
@@ -1336,21 +1340,6 @@ bool jit_available(std::string *why)
 
 std::string jit_pass_source(const plan::Pass &p, bool c64) { return p.tc ? gen_source_tc(p) : gen_source(p, c64); }
 
-namespace {
-// The number before `key` in a ptxas -v report ("Used 128 registers",
-// "44 bytes spill stores"); -1 when absent.
-long ptxas_number(const std::string &log, const char *key)
-{
-    const size_t p = log.find(key);
-    if (p == std::string::npos) return -1;
-    size_t e = p;
-    while (e > 0 && log[e - 1] == ' ') --e;
-    size_t b = e;
-    while (b > 0 && log[b - 1] >= '0' && log[b - 1] <= '9') --b;
-    return b < e ? std::atol(log.c_str() + b) : -1;
-}
-}  // namespace
-
 qv_status jit_compile_host(const std::vector<plan::Pass> &passes, bool c64, int64_t out[4])
 {
     const JitApi &N = api();
@@ -1363,7 +1352,9 @@ qv_status jit_compile_host(const std::vector<plan::Pass> &passes, bool c64, int6
         srcs[i] = jit_pass_source(passes[i], c64);
         bytes += int64_t(srcs[i].size());
     }
-    const size_t nt = std::max<size_t>(1, std::min<size_t>(np, std::max(1u, std::thread::hardware_concurrency())));
+    // as many compiler threads as the kernel loader uses: NVRTC and ptxas take
+    // hundreds of MB of host memory each
+    const size_t nt = std::max<size_t>(1, std::min<size_t>(np, compile_threads()));
     std::atomic<size_t> next{0};
     std::vector<std::thread> th;
     for (size_t t = 0; t < nt; ++t)
@@ -1377,8 +1368,8 @@ qv_status jit_compile_host(const std::vector<plan::Pass> &passes, bool c64, int6
     int64_t regs = 0, spilling = 0;
     for (size_t i = 0; i < np; ++i) {
         if (!ok[i]) return fail(QV_ERR_CUDA, "pass %zu: %s", i, errs[i].c_str());
-        regs = std::max<int64_t>(regs, ptxas_number(logs[i], "registers"));
-        spilling += ptxas_number(logs[i], "bytes spill stores") > 0 ? 1 : 0;
+        regs = std::max<int64_t>(regs, ptxas_registers(logs[i]));
+        spilling += ptxas_spills(logs[i]) ? 1 : 0;
     }
     out[0] = int64_t(np);
     out[1] = bytes;
@@ -1415,7 +1406,7 @@ qv_status get_kernels(qv_state *s, const std::vector<std::string> &srcs, const c
         std::vector<std::vector<char>> cubins(todo.size());
         std::vector<std::string> errs(todo.size());
         std::vector<char> okv(todo.size(), 0);
-        const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        const unsigned hw = compile_threads();
         size_t next = 0;
         std::mutex mu;
         auto worker = [&] {
@@ -1559,9 +1550,12 @@ qv_status jit_prepare(qv_state *s, const std::vector<plan::Pass> &passes, std::s
     return QV_OK;
 }
 
-qv_status jit_launch(qv_state *s, const JitProgram &P)
+qv_status jit_launch(qv_state *s, const JitProgram &P, cudaStream_t on)
 {
     QV_CUDA(cudaSetDevice(s->device));
+    // on a stream of the caller's (a batch graph being captured): no counters, no events
+    const bool count = on == nullptr;
+    CUstream cs = reinterpret_cast<CUstream>(count ? s->stream : on);
     if (P.tc) {
         int *status = nullptr;
         QV_TRY(status_word(s, &status));
@@ -1573,11 +1567,13 @@ qv_status jit_launch(qv_state *s, const JitProgram &P)
             void *amp = s->amp;
             void *mats = static_cast<char *>(P.mats) + P.mat_off[i];
             void *args[] = {&amp, &ntiles, &mats, &status, &spin};
-            prof_bytes(s, QV_K_FUSED, 2.0 * double(dim(s)) * amp_bytes(s->dt));
-            prof_begin(s, QV_K_FUSED);
-            const CUresult r = api().launch(c.fn, grid, 1, 1, unsigned(P.threads[i]), 1, 1, unsigned(c.smem),
-                                            reinterpret_cast<CUstream>(s->stream), args, nullptr);
-            prof_end(s, QV_K_FUSED);
+            if (count) {
+                prof_bytes(s, QV_K_FUSED, 2.0 * double(dim(s)) * amp_bytes(s->dt));
+                prof_begin(s, QV_K_FUSED);
+            }
+            const CUresult r =
+                api().launch(c.fn, grid, 1, 1, unsigned(P.threads[i]), 1, 1, unsigned(c.smem), cs, args, nullptr);
+            if (count) prof_end(s, QV_K_FUSED);
             if (r != CUDA_SUCCESS) return cu_fail(r, "cuLaunchKernel");
         }
         return QV_OK;
@@ -1588,13 +1584,15 @@ qv_status jit_launch(qv_state *s, const JitProgram &P)
         const unsigned grid = unsigned(std::min<uint64_t>(ntiles, uint64_t(c.per_sm) * s->num_sms));
         void *amp = s->amp;
         void *args[] = {&amp, &ntiles, const_cast<uint64_t *>(P.args[i].data())};
-        prof_bytes(s, QV_K_FUSED, 2.0 * double(dim(s)) * amp_bytes(s->dt));
-        prof_begin(s, QV_K_FUSED);
-        const CUresult r = api().launch(c.fn, grid, 1, 1, unsigned(P.threads[i]), 1, 1, unsigned(c.smem),
-                                          reinterpret_cast<CUstream>(s->stream), args, nullptr);
-        prof_end(s, QV_K_FUSED);
+        if (count) {
+            prof_bytes(s, QV_K_FUSED, 2.0 * double(dim(s)) * amp_bytes(s->dt));
+            prof_begin(s, QV_K_FUSED);
+        }
+        const CUresult r =
+            api().launch(c.fn, grid, 1, 1, unsigned(P.threads[i]), 1, 1, unsigned(c.smem), cs, args, nullptr);
+        if (count) prof_end(s, QV_K_FUSED);
         if (r != CUDA_SUCCESS) return cu_fail(r, "cuLaunchKernel");
-        s->prof.h2d += P.args[i].size() * sizeof(uint64_t);
+        if (count) s->prof.h2d += P.args[i].size() * sizeof(uint64_t);
     }
     return QV_OK;
 }

@@ -413,10 +413,11 @@ qv_status qv_plan_source(int n, qv_dtype dt, const qv_gate *g, size_t ng, const 
     return QV_OK;
 }
 
-qv_status qv_dist_plan(int n, int global_bits, int rank, const qv_gate *g, size_t ng, qv_dist_step *steps,
-                       size_t steps_cap, size_t *nsteps, qv_gate *local_gates, size_t gates_cap, size_t *ngates,
-                       int32_t *final_perm)
+qv_status qv_dist_plan(int n, int global_bits, int rank, const qv_gate *g, size_t ng, int32_t flags,
+                       qv_dist_step *steps, size_t steps_cap, size_t *nsteps, qv_gate *local_gates, size_t gates_cap,
+                       size_t *ngates, int32_t *final_perm)
 {
+    if (flags & ~int32_t(QV_DIST_RESTORE)) return fail(QV_ERR_ARG, "unknown flags 0x%x", unsigned(flags));
     if (!nsteps || !ngates) return fail(QV_ERR_ARG, "nsteps or ngates is NULL");
     QV_TRY(check_plan_args(n, QV_C64, g, ng));
     if (global_bits < 1 || global_bits >= n || global_bits > 30)
@@ -425,7 +426,7 @@ qv_status qv_dist_plan(int n, int global_bits, int rank, const qv_gate *g, size_
     std::vector<qv_dist_step> st;
     std::vector<qv_gate> lg;
     std::vector<int32_t> perm;
-    QV_TRY(dist_plan(n, global_bits, rank, g, ng, st, lg, perm));
+    QV_TRY(dist_plan(n, global_bits, rank, g, ng, st, lg, perm, (flags & QV_DIST_RESTORE) != 0));
     *nsteps = st.size();
     *ngates = lg.size();
     if (final_perm) std::copy(perm.begin(), perm.end(), final_perm);

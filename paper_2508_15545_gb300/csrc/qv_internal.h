@@ -148,8 +148,9 @@ qv_status verify_qft(qv_state *s, uint64_t j, double *dist);
 qv_status distance(qv_state *a, qv_state *b, double *out);
 
 // ---------------------------------------------------------------- split states (dist_plan.cpp)
+// restore: steps that bring the qubits back to their natural order follow the circuit
 qv_status dist_plan(int n, int g, int rank, const qv_gate *gates, size_t ng, std::vector<qv_dist_step> &steps,
-                    std::vector<qv_gate> &local_gates, std::vector<int32_t> &final_perm);
+                    std::vector<qv_gate> &local_gates, std::vector<int32_t> &final_perm, bool restore);
 
 // ---------------------------------------------------------------- reductions (reduce_kernels.cu)
 // out[0] = sum |a|^2, out[1 + q] = sum over bit q set of |a|^2, q < n.

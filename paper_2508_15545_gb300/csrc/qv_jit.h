@@ -25,7 +25,9 @@ qv_status jit_compile_host(const std::vector<plan::Pass> &passes, bool c64, int6
 struct JitProgram;
 // Forward passes: compile (or take from the cache) and pack.
 qv_status jit_prepare(qv_state *s, const std::vector<plan::Pass> &passes, std::shared_ptr<JitProgram> &out);
-qv_status jit_launch(qv_state *s, const JitProgram &prog);
+// Launches on the handle's stream (counted in its profile), or on `on` when
+// given (a batch graph being captured: not counted).
+qv_status jit_launch(qv_state *s, const JitProgram &prog, cudaStream_t on = nullptr);
 // Adjoint passes (see jit_run_adjoint).
 qv_status jit_prepare_adjoint(qv_state *s, const std::vector<plan::Pass> &passes, std::shared_ptr<JitProgram> &out);
 qv_status jit_launch_adjoint(qv_state *s, const JitProgram &prog, void *lam, double *part, int G);

@@ -490,6 +490,26 @@ extern "C" qv_status qv_zsums_noalloc(const void *dev_amp, int n, qv_dtype dt, v
         return fail(QV_ERR_ARG, "qv_zsums_noalloc: n = %d outside [1, %d] (its fixed scratch holds the partials of "
                                 "at most 2^%d amplitudes)", n, kStaticMaxN, kStaticMaxN);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // the fixed array belongs to the current device: the buffers and the stream must too
+    int dev = 0;
+    QV_CUDA(cudaGetDevice(&dev));
+    for (const void *p : {dev_amp, static_cast<const void *>(dev_out)}) {
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(QV_ERR_ARG, "qv_zsums_noalloc: %p is not memory CUDA knows", p);
+        }
+        if (a.type == cudaMemoryTypeDevice && a.device != dev)
+            return fail(QV_ERR_ARG, "qv_zsums_noalloc: buffer %p is on device %d, the current device is %d", p,
+                        a.device, dev);
+    }
+    if (st) {
+        int sdev = dev;
+        if (cudaStreamGetDevice(st, &sdev) == cudaSuccess && sdev != dev)
+            return fail(QV_ERR_ARG, "qv_zsums_noalloc: the stream belongs to device %d, the current device is %d",
+                        sdev, dev);
+        (void)cudaGetLastError();
+    }
     return dt == QV_C64 ? zsums_noalloc_impl<float>(dev_amp, n, st, dev_out)
                         : zsums_noalloc_impl<double>(dev_amp, n, st, dev_out);
 }

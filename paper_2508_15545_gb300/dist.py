@@ -40,12 +40,14 @@ def exchange_half(shard, peer: int, send_upper: bool, group=None):
     mine.copy_(recv)
 
 
-def run_schedule(n: int, rank: int, world: int, gates, shard, apply_local: Callable, group=None) -> List[int]:
+def run_schedule(n: int, rank: int, world: int, gates, shard, apply_local: Callable, group=None,
+                 restore: bool = False) -> List[int]:
     """Runs ``gates`` on this rank's ``shard``: local steps through
     ``apply_local((gate array, count))``, exchanges with ``exchange_half``.
-    Returns final_perm (logical qubit q sits at physical qubit final_perm[q])."""
+    Returns final_perm (logical qubit q sits at physical qubit final_perm[q];
+    the identity with ``restore``)."""
     g = global_bits(world)
-    steps, (lg, _), perm = qv.qv_dist_plan(n, g, rank, gates)
+    steps, (lg, _), perm = qv.qv_dist_plan(n, g, rank, gates, restore)
     import ctypes
     base = ctypes.addressof(lg)
     size = ctypes.sizeof(qv.qv_gate)
@@ -81,14 +83,16 @@ class DistState:
         self.h = qv.qv_wrap(self.shard.data_ptr(), self.L, qv.QV_C64, torch.cuda.current_stream())
         self.perm = list(range(n))
 
-    def apply(self, gates, mode: int = qv.QV_MODE_AUTO):
-        """Applies ``gates`` (logical qubits) from the current qubit order
-        (identity only: call on a freshly created state or after restore)."""
+    def apply(self, gates, mode: int = qv.QV_MODE_AUTO, restore: bool = True):
+        """Applies ``gates`` (logical qubits) from the natural qubit order; with
+        ``restore`` (the default) the state ends in the natural order again,
+        else ``perm`` says where each logical qubit sits and the next apply()
+        refuses to start."""
         if self.perm != list(range(self.n)):
             raise RuntimeError("apply() starts from the natural qubit order")
         flat = self.shard.view(-1)
         self.perm = run_schedule(self.n, self.rank, self.world, gates, flat,
-                                 lambda arr: qv.qv_apply_circuit(self.h, arr, mode), self.group)
+                                 lambda arr: qv.qv_apply_circuit(self.h, arr, mode), self.group, restore)
 
     def close(self):
         if self.h:

@@ -116,7 +116,7 @@ def _load():
         "qv_plan_compile": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(qv_gate), ctypes.c_size_t,
                             ctypes.POINTER(qv_plan_opts), ctypes.POINTER(ctypes.c_int64)],
         "qv_dist_plan": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(qv_gate), ctypes.c_size_t,
-                         ctypes.POINTER(qv_dist_step), ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t),
+                         ctypes.c_int32, ctypes.POINTER(qv_dist_step), ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t),
                          ctypes.POINTER(qv_gate), ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t),
                          ctypes.POINTER(ctypes.c_int32)],
         "qv_plan_tc_stage": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(qv_gate), ctypes.c_size_t,
@@ -372,7 +372,10 @@ def qv_plan_tc_stage(n: int, gates, pass_index: int, stage: int, tile_bits: int 
             "has_matrix": bool(o.has_matrix), "ext": int(o.ext), "m": m}
 
 
-def qv_dist_plan(n: int, global_bits: int, rank: int, gates):
+QV_DIST_RESTORE = 1
+
+
+def qv_dist_plan(n: int, global_bits: int, rank: int, gates, restore: bool = False):
     """Schedule of ``gates`` on ``rank`` of 2^global_bits ranks (Eq. 9; host
     only): (steps, local gate array, final_perm). steps: list of dicts with
     kind 'local' (begin, end into the local gate array) or 'exchange' (peer,
@@ -382,11 +385,13 @@ def qv_dist_plan(n: int, global_bits: int, rank: int, gates):
     else:
         arr, ng = gates_to_c(gates), len(gates)
     ns, nl = ctypes.c_size_t(), ctypes.c_size_t()
-    _check(lib.qv_dist_plan(n, global_bits, rank, arr, ng, None, 0, ctypes.byref(ns), None, 0, ctypes.byref(nl), None))
+    fl = QV_DIST_RESTORE if restore else 0
+    _check(lib.qv_dist_plan(n, global_bits, rank, arr, ng, fl, None, 0, ctypes.byref(ns), None, 0, ctypes.byref(nl),
+                            None))
     st = (qv_dist_step * max(1, ns.value))()
     lg = (qv_gate * max(1, nl.value))()
     perm = (ctypes.c_int32 * n)()
-    _check(lib.qv_dist_plan(n, global_bits, rank, arr, ng, st, ns.value, ctypes.byref(ns), lg, nl.value,
+    _check(lib.qv_dist_plan(n, global_bits, rank, arr, ng, fl, st, ns.value, ctypes.byref(ns), lg, nl.value,
                             ctypes.byref(nl), perm))
     steps = []
     for k in range(ns.value):

@@ -46,7 +46,7 @@ def _to_gates(arr_ng):
     return out
 
 
-def _rank(rank, world, port, n, seed, q):
+def _rank(rank, world, port, n, seed, restore, q):
     import torch
     import torch.distributed as dist
     sys.path.insert(0, ROOT)
@@ -64,7 +64,7 @@ def _rank(rank, world, port, n, seed, q):
         def local(arr_ng):
             O.run(L, _to_gates(arr_ng), shard)
 
-        perm = D.run_schedule(n, rank, world, gates, t, local)
+        perm = D.run_schedule(n, rank, world, gates, t, local, restore=restore)
         parts = [torch.empty_like(t) for _ in range(world)] if rank == 0 else None
         dist.gather(t, parts, dst=0)
         if rank == 0:
@@ -88,13 +88,14 @@ def _logical(phys, perm):
     return phys[src]
 
 
+@pytest.mark.parametrize("restore", [False, True])
 @pytest.mark.parametrize("world,n", [(2, 9), (4, 10)])
-def test_split_state_matches_oracle(orc, world, n):
+def test_split_state_matches_oracle(orc, world, n, restore):
     seed = 40 + world
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank, args=(r, world, port, n, seed, q)) for r in range(world)]
+    procs = [ctx.Process(target=_rank, args=(r, world, port, n, seed, restore, q)) for r in range(world)]
     for p in procs:
         p.start()
     res = [q.get(timeout=300) for _ in range(world)]
@@ -105,6 +106,8 @@ def test_split_state_matches_oracle(orc, world, n):
     assert not errs, errs
     perms = [r[2] for r in res]
     assert all(p == perms[0] for p in perms)                # every rank ends in the same qubit order
+    if restore:
+        assert perms[0] == list(range(n))                    # back in the natural order
     phys = next(r[1] for r in res if r[1] is not None)
     from paper_2508_15545_gb300 import workloads as W
     want = orc.run(n, _circuit(n, seed), W.random_state(n, seed))

@@ -181,3 +181,29 @@ def test_autotune_schedule_variants(qvlib, orc, cuda):
         assert np.linalg.norm(qv.qv_get_state(h).astype(complex) - orc.run(n, g)) <= 1e-5
     finally:
         qv.qv_destroy(h)
+
+
+def test_batch_large_member_runs_its_own_passes(qvlib, orc, cuda):
+    """A member that fills the GPU alone (24 qubits: 2^13 tiles per pass) runs
+    on its own compiled fused passes inside the batch graph; the small members
+    stay in the persistent queue. Every state equals the oracle's, <H> too."""
+    qv = qvlib
+    spec = [(24, 4), (12, 5), (13, 3)]
+    circuits = [W.random_circuit(n, d, seed=2400 + k) for k, (n, d) in enumerate(spec)]
+    terms = [(1.0, 0, 0b11), (0.5, 0b1, 0)]
+    states = [qv.qv_create(n, 0) for n, _ in spec]
+    try:
+        b = qv.Batch(list(zip(states, circuits)), terms)
+        info = b.info()
+        big = [g for g in info if g["compiled"] == 2]
+        assert len(big) == 1 and big[0]["qubits"] == 24 and big[0]["circuits"] == 1
+        for rep in range(2):
+            e = b.run()
+            for (n, _), h, g, ek in zip(spec, states, circuits, e):
+                want = orc.run(n, g)
+                assert np.linalg.norm(qv.qv_get_state(h).astype(complex) - want) <= 1e-5, (n, rep)
+                assert ek == pytest.approx(orc.expect_terms(want, terms), abs=2e-5), (n, rep)
+        b.close()
+    finally:
+        for h in states:
+            qv.qv_destroy(h)

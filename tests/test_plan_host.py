@@ -2,6 +2,7 @@
 algorithmic cost model (HBM bytes, floating-point operations) that the
 roofline of a fused pass is measured against."""
 import math
+import os
 
 import pytest
 
@@ -150,3 +151,32 @@ def test_plan_source_rejects_bad_args(qv):
     with pytest.raises(qv.QvError) as e:
         qv.qv_plan_source(12, 0, g, 0, flags=qv.QV_PLAN_INTERPRET)
     assert e.value.status == qv.QV_ERR_ARG
+
+
+def test_ptxas_report_reads_every_function(tmp_path):
+    """The ptxas -v report of a module with two functions: the largest register
+    count counts, and a spill in either function marks the pass as spilling."""
+    import subprocess
+    import textwrap
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                       "paper_2508_15545_gb300", "csrc", "ptxas_report.h")
+    src = tmp_path / "t.cpp"
+    src.write_text(textwrap.dedent('''
+        #include "%s"
+        #include <cstdio>
+        int main() {
+            const std::string two =
+                "ptxas info    : Compiling entry function 'helper' for 'sm_103a'\\n"
+                "    0 bytes stack frame, 0 bytes spill stores, 0 bytes spill loads\\n"
+                "ptxas info    : Used 40 registers, used 0 barriers\\n"
+                "ptxas info    : Compiling entry function 'qv_pass' for 'sm_103a'\\n"
+                "    32 bytes stack frame, 64 bytes spill stores, 32 bytes spill loads\\n"
+                "ptxas info    : Used 128 registers, used 1 barriers\\n";
+            const std::string clean = "    0 bytes spill stores\\nptxas info    : Used 96 registers\\n";
+            std::printf("%%ld %%d %%ld %%d %%ld\\n", qv::ptxas_registers(two), int(qv::ptxas_spills(two)),
+                        qv::ptxas_registers(clean), int(qv::ptxas_spills(clean)), qv::ptxas_registers("nothing"));
+        }
+    ''' % hdr))
+    exe = tmp_path / "t"
+    subprocess.check_call(["g++", "-std=c++17", "-O1", "-o", str(exe), str(src)])
+    assert subprocess.check_output([str(exe)]).decode().split() == ["128", "1", "96", "0", "-1"]

@@ -58,3 +58,41 @@ def test_noalloc_rejects_sizes_beyond_its_limit(qvlib, cuda):
     assert e.value.status == qv.QV_ERR_ARG and "outside [1, 30]" in str(e.value)
     with pytest.raises(qv.QvError):
         qv.qv_zsums_noalloc(0, 4, qv.QV_C64, None, out.data_ptr())
+
+
+def test_noalloc_after_a_larger_call_reads_only_its_own_partials(qvlib, cuda):
+    """A 26-qubit call fills more of the fixed array than a 20-qubit call on
+    another state uses next; the smaller call must still give its own sums."""
+    qv, torch = qvlib, cuda
+    stream = torch.cuda.current_stream()
+    big, small = qv.qv_create(26, 0, stream), qv.qv_create(20, 0, stream)
+    try:
+        qv.qv_apply_circuit(big, W.random_circuit(26, 2, 5), mode=qv.QV_MODE_PLAIN)
+        qv.qv_apply_circuit(small, W.random_circuit(20, 2, 6), mode=qv.QV_MODE_PLAIN)
+        for h in (big, small):
+            sums = _noalloc_sums(qv, torch, h)
+            ez, _ = qv.qv_expect_z(h)
+            assert sums[0] == pytest.approx(qv.qv_norm2(h), abs=1e-7)
+            assert np.max(np.abs((sums[0] - 2 * sums[1:]) - ez)) <= 2e-7
+    finally:
+        qv.qv_destroy(big)
+        qv.qv_destroy(small)
+
+
+def test_noalloc_at_its_limit_30_qubits(qvlib, cuda):
+    """n = 30, the largest size the fixed array holds (all 65,536 blocks of
+    partials), complex64, against qv_expect_z on the same state."""
+    qv, torch = qvlib, cuda
+    free, _ = torch.cuda.mem_get_info()
+    if free < (8 << 30) + (2 << 30):
+        pytest.skip("needs 10 GiB of free device memory")
+    h = qv.qv_create(30, 0, torch.cuda.current_stream())
+    try:
+        qv.qv_apply_circuit(h, W.random_circuit(30, 1, 9), mode=qv.QV_MODE_FUSED)
+        sums = _noalloc_sums(qv, torch, h)
+        ez, _ = qv.qv_expect_z(h)
+        assert sums[0] == pytest.approx(qv.qv_norm2(h), abs=1e-7)
+        assert np.max(np.abs((sums[0] - 2 * sums[1:]) - ez)) <= 2e-7
+    finally:
+        qv.qv_destroy(h)
+
