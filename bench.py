@@ -494,24 +494,36 @@ def extras(args, qv, torch, dev, h64, gates):
         res["sampling"] = {"shots": len(u), "ms": ms_s, "shots_per_s": len(u) / (ms_s / 1e3)}
     except Exception as e:  # noqa: BLE001
         res["sampling"] = {"error": str(e)}
-    # 1c. the same step with the state in mapped host memory (read and written over NVLink-C2C)
+    # 1c. the same step with the state in mapped host memory: staged through a device window
+    # (one copy in and one out per step) and, for comparison, read and written in place over
+    # NVLink-C2C by every pass
     try:
         hh = qv.qv_create(args.n, qv.QV_C64, flags=qv.QV_ALLOC_HOST)
         garr = qv.gates_to_c(gates)
 
-        def host_step():
+        def host_step(flags=0):
             qv.qv_set_basis(hh, 0)
-            qv.qv_apply_circuit(hh, (garr, len(gates)), qv.QV_MODE_FUSED)
-        ms_h = _timed(torch, dev, host_step, 1)
-        # the passes of the plan that ran (host states take their own tile size): counted launches
+            qv.qv_apply_circuit(hh, (garr, len(gates)), qv.QV_MODE_FUSED, 0, flags)
+        ms_w = _timed(torch, dev, host_step, 2)
         qv.qv_profile(hh, timing=False)
         host_step()
         torch.cuda.synchronize(dev)
+        h2d_w, d2h_w = qv.qv_transfer_bytes(hh)
+        ms_h = _timed(torch, dev, lambda: host_step(qv.QV_PLAN_HOST_IN_PLACE), 1)
+        # the passes of the in-place plan (host states take their own tile size): counted launches
+        qv.qv_profile(hh, timing=False)
+        host_step(qv.QV_PLAN_HOST_IN_PLACE)
+        torch.cuda.synchronize(dev)
         passes = int(qv.qv_profile_read(hh)["fused"][0])
         qv.qv_profile(hh, timing=False)
-        res["host_memory_state"] = {"ms_per_step": ms_h, "updates_per_s": len(gates) * N / (ms_h / 1e3),
-                                    "passes": passes,
-                                    "GBps_over_c2c": 2.0 * passes * N * 8 / (ms_h / 1e3) / 1e9}
+        res["host_memory_state"] = {
+            "window": {"ms_per_step": ms_w, "updates_per_s": len(gates) * N / (ms_w / 1e3),
+                       "c2c_bytes_per_step": h2d_w + d2h_w,
+                       "note": "the whole state staged into one device window: one copy in, every pass in HBM, "
+                               "one copy back"},
+            "in_place": {"ms_per_step": ms_h, "updates_per_s": len(gates) * N / (ms_h / 1e3), "passes": passes,
+                         "c2c_bytes_per_step": 2 * passes * N * 8,
+                         "GBps_over_c2c": 2.0 * passes * N * 8 / (ms_h / 1e3) / 1e9}}
         qv.qv_destroy(hh)
     except Exception as e:  # noqa: BLE001
         res["host_memory_state"] = {"error": str(e)}
@@ -694,24 +706,25 @@ def extras(args, qv, torch, dev, h64, gates):
             qv.qv_destroy(hh)
     except Exception as e:  # noqa: BLE001
         res["batch_ansatz"] = {"error": str(e)}
-    # 5. uneven batch: 64 random circuits, 16..28 qubits, depth 10..60, one persistent
-    # launch per tile size, tile size autotuned per qubit count at creation (last: the
-    # tuning sets the default tile size of those qubit counts for the rest of the process)
+    # 5. uneven batch: 64 random circuits, 16..28 qubits, depth 10..60, in one graph: the
+    # members that fill the GPU alone on their own compiled passes, the rest in one
+    # persistent launch per tile size
     try:
         spec = W.uneven_batch(64, W.config_seed(4))
         circs = [W.random_circuit(n_u, d_u, s_u) for n_u, d_u, s_u in spec]
         hs_u = [qv.qv_create(n_u, qv.QV_C64) for n_u, _, _ in spec]
         t0 = time.perf_counter()
-        bu = qv.Batch(list(zip(hs_u, circs)), flags=qv.QV_PLAN_AUTOTUNE)
+        bu = qv.Batch(list(zip(hs_u, circs)))
         create_s = time.perf_counter() - t0
         ms_u = _timed(torch, dev, bu.run, 2)
         upd = sum(len(c) * (1 << n_u) for c, (n_u, _, _) in zip(circs, spec))
+        groups = bu.info()
         res["uneven_batch"] = {"workload": "64 random circuits, qubits uniform in [16, 28], depth uniform in [10, 60], "
                                            "complex64", "ms_per_batch": ms_u, "updates_per_s": upd / (ms_u / 1e3),
-                               "create_s_with_autotune": create_s,
-                               "tile_bits_per_qubits": {str(n_u): qv.qv_default_tile_bits(n_u, qv.QV_C64)
-                                                        for n_u in sorted({x[0] for x in spec})},
-                               "launch_groups": bu.info()}
+                               "create_s": create_s,
+                               "tile_bits_per_qubits": {str(g["qubits"]): g["tile_bits"] for g in groups},
+                               "members_on_own_passes": sum(1 for g in groups if g["compiled"] == 2),
+                               "queued_groups": [g for g in groups if g["compiled"] != 2]}
         bu.close()
         for hh in hs_u:
             qv.qv_destroy(hh)

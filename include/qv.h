@@ -89,6 +89,9 @@ typedef enum {
 #define QV_PLAN_NO_PAIRS 4   /* fused mode: no 4x4 operations on two register qubits (the
                                 compiled complex64 kernel merges runs of operations on two
                                 qubits into one 4x4 when that takes fewer FP32 operations) */
+#define QV_PLAN_HOST_IN_PLACE 32  /* fused mode, state in host memory: every pass reads and writes
+                                the host memory in place over the host link instead of running in
+                                a device window */
 #define QV_PLAN_AUTOTUNE 16  /* qv_batch_create: run the autotuner once for every qubit count of
                                 the batch that has no tuned tile size yet (on the first state of
                                 that size with its circuit; the batch run resets the states) */
@@ -101,7 +104,10 @@ typedef struct {
     int32_t mode;        /* qv_mode */
     int32_t tile_bits;   /* fused: log2 of the tile size in amplitudes (0 = default) */
     int32_t flags;       /* QV_PLAN_* bits */
-    int32_t reserved[5]; /* set to 0 */
+    int32_t window_bits; /* fused, state in host memory (QV_ALLOC_HOST): log2 of the amplitudes of
+                            the device window it is staged through (0 = default: the whole state
+                            when it takes at most half of the free device memory) */
+    int32_t reserved[4]; /* set to 0 */
 } qv_plan_opts;
 
 /* One Pauli string times a real coefficient: X on the qubits set only in

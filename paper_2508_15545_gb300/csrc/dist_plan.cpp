@@ -42,8 +42,12 @@ qv_status dist_plan(int n, int g, int rank, const qv_gate *gates, size_t ng, std
     steps.clear();
     lg.clear();
     size_t seg_begin = 0;
+    // gates of the circuit in the current segment, counted the same way on every
+    // rank: a segment whose gates all fall away on this rank (controls that are 0
+    // here) still gives an (empty) step, so every rank has the same steps
+    size_t pending = 0;
     auto flush = [&]() {
-        if (lg.size() > seg_begin) {
+        if (pending > 0 || lg.size() > seg_begin) {
             qv_dist_step s{};
             s.kind = QV_DIST_LOCAL;
             s.gate_begin = seg_begin;
@@ -51,6 +55,7 @@ qv_status dist_plan(int n, int g, int rank, const qv_gate *gates, size_t ng, std
             steps.push_back(s);
         }
         seg_begin = lg.size();
+        pending = 0;
     };
     auto needs_local = [&](const qv_gate &x, cd U[4]) {
         if (x.kind == QV_G_SWAP) return false;
@@ -81,6 +86,7 @@ qv_status dist_plan(int n, int g, int rank, const qv_gate *gates, size_t ng, std
         s.ctrl = -1;
         s.param[0] = s.param[1] = s.param[2] = -1;
         lg.push_back(s);
+        ++pending;
         swap_labels(pa, pb);
     };
     auto exchange = [&](int pg) {  // global position pg <-> local position L - 1
@@ -119,6 +125,7 @@ qv_status dist_plan(int n, int g, int rank, const qv_gate *gates, size_t ng, std
             exchange(pg);
         }
         // the gate on this rank
+        ++pending;
         qv_gate y = x;
         const int pt = perm[x.target];
         int pc = x.ctrl >= 0 ? perm[x.ctrl] : -1;

@@ -265,6 +265,7 @@ qv_status qv_destroy(qv_state *s)
 {
     if (!s) return QV_OK;
     cudaError_t e = cudaStreamSynchronize(s->stream);
+    window_release(s);
     plan_cache_release(s);
     adjoint_release(s);
     prof_release(s);

@@ -36,6 +36,7 @@ struct Prof {
 };
 
 struct PlanCache;       // fused-pass buffers (fused.cu)
+struct HostWindow;      // device windows of a state in host memory (window.cu)
 struct AdjointBuffers;  // lambda buffer and gradient partials (adjoint.cu)
 
 }  // namespace qv
@@ -56,6 +57,7 @@ struct qv_state {
     qv::PlanCache *plan = nullptr;
     qv::AdjointBuffers *adj = nullptr;
     int *dev_status = nullptr;    // device status word written by kernels with bounded waits
+    qv::HostWindow *window = nullptr;  // host-memory states: device windows the passes run in
 };
 
 namespace qv {

@@ -27,6 +27,10 @@ qv_status plan_compile(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv
 qv_status plan_tc_stage(int n, qv_dtype dt, const qv_gate *g, size_t ng, const qv_plan_opts *opts, int pass,
                         int stage, qv_tc_stage *out);
 
+// A state in host memory: the circuit runs in device windows (window.cu).
+qv_status apply_windowed(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_opts *opts);
+void window_release(qv_state *s);
+
 // Bit q of every index moves to bit perm[q].
 qv_status apply_permutation(qv_state *s, const int32_t *perm);
 // Frees per-handle planning buffers.

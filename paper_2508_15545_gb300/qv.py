@@ -23,6 +23,7 @@ QV_PLAN_INTERPRET = 2
 QV_PLAN_NO_PAIRS = 4
 QV_PLAN_TENSOR = 8
 QV_PLAN_AUTOTUNE = 16
+QV_PLAN_HOST_IN_PLACE = 32
 QV_ALLOC_HOST = 1
 QV_SWEEP_AUTO, QV_SWEEP_PER_GATE, QV_SWEEP_TILES, QV_SWEEP_COMPILED = 0, 1, 2, 3
 STATUS_NAMES = {0: "QV_OK", 1: "QV_ERR_ARG", 2: "QV_ERR_OOM", 3: "QV_ERR_CUDA",
@@ -49,7 +50,7 @@ class qv_gate(ctypes.Structure):
 
 class qv_plan_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("tile_bits", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("window_bits", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class qv_tc_stage(ctypes.Structure):

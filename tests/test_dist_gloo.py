@@ -145,6 +145,14 @@ def test_schedule_pairs_ranks_consistently(qvlib, g):
     for r in range(1 << g):
         steps, _, _ = qv.qv_dist_plan(n, g, r, diag)
         assert all(s["kind"] == "local" for s in steps)
+    # a segment whose gates are all controlled by a global qubit is empty on the
+    # ranks where that qubit is 0, but still a step there
+    gated = [W.Gate("u3", 2, ctrl=n - 1, theta=(0.4, 0.1, 0.2)), W.Gate("x", 1, ctrl=n - 1), W.Gate("h", n - 1),
+             W.Gate("u3", 3, ctrl=n - 2, theta=(0.3, 0.2, 0.1))]
+    seqs = [qv.qv_dist_plan(n, g, r, gated)[0] for r in range(1 << g)]
+    assert all([s["kind"] for s in q] == [s["kind"] for s in seqs[0]] for q in seqs)
+    size = [q[0]["end"] - q[0]["begin"] for q in seqs]
+    assert size[0] < size[-1]            # the controlled gates fell away on rank 0, the step did not
 
 
 def test_schedule_rejects_bad_arguments(qvlib):
