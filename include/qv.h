@@ -105,8 +105,10 @@ typedef struct {
     int32_t tile_bits;   /* fused: log2 of the tile size in amplitudes (0 = default) */
     int32_t flags;       /* QV_PLAN_* bits */
     int32_t window_bits; /* fused, state in host memory (QV_ALLOC_HOST): log2 of the amplitudes of
-                            the device window it is staged through (0 = default: the whole state
-                            when it takes at most half of the free device memory) */
+                            the device windows it is staged through; below n the state streams
+                            through two windows in chunks (the split schedule of qv_dist_plan).
+                            0 = default: the whole state as one window when it takes at most half
+                            of the free device memory, else passes in place */
     int32_t reserved[4]; /* set to 0 */
 } qv_plan_opts;
 

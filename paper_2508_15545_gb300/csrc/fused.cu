@@ -290,7 +290,9 @@ qv_status apply_fused(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_op
     if (ng == 0) return QV_OK;
     if (opts && opts->window_bits && (opts->window_bits < plan::kMinK || opts->window_bits > s->n))
         return fail(QV_ERR_ARG, "window_bits %d outside [%d, n = %d]", opts->window_bits, plan::kMinK, s->n);
-    if (s->host_mem && !(opts && (opts->flags & QV_PLAN_HOST_IN_PLACE))) return apply_windowed(s, g, ng, opts);
+    if (s->host_mem && !(opts && (opts->flags & QV_PLAN_HOST_IN_PLACE)) &&
+        ((opts && opts->window_bits) || default_window_bits(s) > 0))
+        return apply_windowed(s, g, ng, opts);
     int K = (opts && opts->tile_bits) ? opts->tile_bits : default_tile_bits(s, opts);
     if (K < plan::kMinK || K > plan::kMaxK) return fail(QV_ERR_ARG, "tile_bits %d outside [10, 12]", K);
     if (K > s->n) return fail(QV_ERR_ARG, "tile_bits %d exceeds n = %d", K, s->n);

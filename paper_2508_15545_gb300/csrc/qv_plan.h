@@ -30,6 +30,9 @@ qv_status plan_tc_stage(int n, qv_dtype dt, const qv_gate *g, size_t ng, const q
 // A state in host memory: the circuit runs in device windows (window.cu).
 qv_status apply_windowed(qv_state *s, const qv_gate *g, size_t ng, const qv_plan_opts *opts);
 void window_release(qv_state *s);
+// The window a host-memory state takes without window_bits: the whole state
+// when it fits in half of the free device memory, else 0 (passes in place).
+int default_window_bits(const qv_state *s);
 
 // Bit q of every index moves to bit perm[q].
 qv_status apply_permutation(qv_state *s, const int32_t *perm);
