@@ -852,6 +852,8 @@ qv_status adjoint_sweep_compiled(qv_state *s, const qv_gate *g, size_t ng, const
         for (int d = 0; d < p.nd; ++d)
             for (int e = 0; e < 4; ++e) p.dU[d][e] = dU[d][e];
         p.cls = p.nd > 0 ? plan::G_GEN : plan::classify(p.U);
+        if (p.nd == 1 && G1.param[0] >= 0)
+            p.gen = G1.kind == QV_G_RX ? 1 : G1.kind == QV_G_RY ? 2 : G1.kind == QV_G_RZ ? 3 : G1.kind == QV_G_P ? 4 : 0;
         pg.push_back(p);
     }
     std::vector<plan::Pass> passes;

@@ -211,6 +211,38 @@ template <int J, int C, int S> QI float gd_reg(const u64 (&r)[8], const u64 (&i)
     }
     float a0, a1; upk(acc, a0, a1); return a0 + a1;
 }
+// adjoint, generator form: the derivative term Re <lambda | dU psi'> of a gate
+// U = exp(-i theta G / 2), psi' = U^dagger psi, equals Im <lambda | G psi> / 2 with psi
+// before the gate is undone (GEN = 1, 2, 3: G = X, Y, Z); for P(theta) (GEN = 4,
+// dP = i |1><1| P) it is -Im <lambda_1 | psi_1>. Sums over the pairs along
+// register bit J (with select bit C == S when C >= 0); (a, b) = (bit 0, bit 1).
+template <int J, int C, int S, int GEN> QI float gg_reg(const u64 (&r)[8], const u64 (&i)[8], const u64 (&lr)[8],
+                                                        const u64 (&li)[8]) {
+    u64 p = 0ull, m = 0ull;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        if ((v >> J) & 1) continue;
+        if (C >= 0 && ((v >> C) & 1) != S) continue;
+        const int w = v | (1 << J);
+        if (GEN == 1) {        // Im(conj(la) pb + conj(lb) pa)
+            p = f2fma(lr[v], i[w], f2fma(lr[w], i[v], p));
+            m = f2fma(li[v], r[w], f2fma(li[w], r[v], m));
+        } else if (GEN == 2) { // Re(conj(lb) pa - conj(la) pb)
+            p = f2fma(lr[w], r[v], f2fma(li[w], i[v], p));
+            m = f2fma(lr[v], r[w], f2fma(li[v], i[w], m));
+        } else if (GEN == 3) { // Im(conj(la) pa - conj(lb) pb)
+            p = f2fma(lr[v], i[v], f2fma(li[w], r[w], p));
+            m = f2fma(li[v], r[v], f2fma(lr[w], i[w], m));
+        } else {               // -Im(conj(lb) pb)
+            p = f2fma(li[w], r[w], p);
+            m = f2fma(lr[w], i[w], m);
+        }
+    }
+    float p0, p1, m0, m1;
+    upk(p, p0, p1); upk(m, m0, m1);
+    const float d = (p0 + p1) - (m0 + m1);
+    return GEN == 4 ? d : 0.5f * d;
+}
 // real 2x2 (imaginary parts zero): (re, re) pairs of U00 U01 U10 U11 at c[0], c[3], c[6], c[9]
 QI void ap2r(const u64 (&c)[12], u64 &ar, u64 &ai, u64 &br, u64 &bi) {
     const u64 xr = ar, xi = ai, yr = br, yi = bi;
@@ -1130,9 +1162,15 @@ void emit_adj_op_c64(std::ostream &o, const plan::Op &op, int O, int lslot)
     // a runtime select (control on a thread bit or outside the tile) skips the op where it is 0;
     // register selects are resolved inside the op
     const std::string cond = C < 0 ? std::string("s || ") + (op.m0id ? "0" : "1") : std::string("1");
-    o << "      if (" << cond << ") { " << coef_load(O, C < 0 ? "s" : std::to_string(s), 12, false)
-      << "\n        " << apply << "\n";
-    for (int d = 0; d < op.nd; ++d) {
+    // generator form (a register target, no lane select): the derivative from psi before the
+    // gate is undone, no derivative matrix
+    const bool gen = op.nd == 1 && op.gen > 0 && J < 3 && C != 3;
+    o << "      if (" << cond << ") { ";
+    if (gen)
+        o << "gsum[0] = gg_reg<" << J << ", " << (C >= 0 ? C : -1) << ", " << (C >= 0 ? 1 : 0) << ", " << op.gen
+          << ">(r, i, rl, il);\n        ";
+    o << coef_load(O, C < 0 ? "s" : std::to_string(s), 12, false) << "\n        " << apply << "\n";
+    for (int d = 0; d < op.nd && !gen; ++d) {
         o << "        { u64 dc[12];";
         for (int e = 0; e < 12; ++e) o << " dc[" << e << "] = cf.c[" << O + 24 + 12 * d + e << "];";
         o << " gsum[" << d << "] = " << grad << "(r, i, rl, il, dc); }\n";

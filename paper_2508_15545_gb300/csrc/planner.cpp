@@ -893,6 +893,7 @@ bool make_plan(int n, int k, bool pin0, bool fuse, bool pairs, const std::vector
                 if (c >= 0) coord(c, op.sreg, op.sthr, op.sext);
                 op.nd = g.nd;
                 op.slot = g.slot;
+                op.gen = g.gen;
                 for (int d = 0; d < g.nd; ++d)
                     for (int e = 0; e < 4; ++e) op.D[d][e] = g.dU[d][e];
                 open_op[t] = g.nd > 0 ? -1 : int(ops.size());  // nothing merges into a differentiated op

@@ -45,6 +45,10 @@ struct PGate {
     // op of its own (class G_GEN), never merged with other gates.
     int nd = 0, slot = -1;
     std::complex<double> dU[3][4];
+    // Adjoint plans: the gate is exp(-i theta G / 2) (gen 1, 2, 3: G = X, Y, Z on
+    // the target) or P(theta) (gen 4: dP = i |1><1| P) in its one trainable angle, so
+    // its derivative term can be taken from psi before the gate is undone; 0: use dU
+    int gen = 0;
 };
 
 enum OpType : int8_t { OP_GEN = 0, OP_X = 1, OP_DIAG = 2, OP_GEN2 = 3 };
@@ -72,6 +76,7 @@ struct Op {
     std::complex<double> M4[16];    // GEN2 only
     int nd = 0, slot = -1;          // adjoint plans: derivatives of this op's gate (see PGate)
     std::complex<double> D[3][4];   // derivative matrices, applied where M[1] applies
+    int gen = 0;                    // adjoint plans: generator form of the derivative (see PGate)
 };
 
 struct Layout {
