@@ -1,9 +1,11 @@
 // Batched circuits: many states, each with its own circuit (same or uneven
-// qubit counts), run as one persistent launch per tile size and captured,
-// together with the per-state initialisation and the batched <H>
-// reduction, in one CUDA graph that is replayed by qv_batch_run.
+// qubit counts), captured together with the per-state initialisation and the
+// batched <H> reduction in one CUDA graph that is replayed by qv_batch_run.
+// Members with enough tiles per pass run their own compiled fused passes, on
+// side streams of the graph so that their kernels share the GPU; the others
+// run as one persistent launch per tile size.
 //
-// Work items are (circuit, pass, chunk of tiles) in round order: every
+// Persistent launches: work items are (circuit, pass, chunk of tiles) in round order: every
 // circuit's pass 0, then every circuit's pass 1, ... (larger circuits first
 // within a round). A CTA claims items with an atomic counter; before a pass-p
 // item of circuit c it waits until all chunks of pass p-1 of c are done
@@ -24,6 +26,13 @@ namespace qv {
 namespace {
 
 constexpr uint32_t kChunkTiles = 32;    // tiles per work item
+// A circuit whose passes have at least 2^kSoloTileBits tiles (and that shares
+// its gate structure with another member, else 2^12 tiles) runs on its own
+// compiled passes (coefficients as kernel parameters, the next tile held in
+// registers); such circuits are spread over kSideStreams capture streams so
+// that their kernels share the GPU.
+constexpr int kSoloTileBits = 8;
+constexpr int kSideStreams = 16;
 constexpr uint32_t kSpinLimit = 1u << 24;  // ~ seconds of __nanosleep(128) before giving up
 
 struct BPass {
@@ -272,6 +281,8 @@ struct qv_batch {
         std::shared_ptr<qv::JitProgram> prog;
     };
     std::vector<Solo> solo;
+    std::vector<cudaStream_t> side;  // capture streams of the solo circuits
+    std::vector<cudaEvent_t> side_ev;  // fork event, then one join event per side stream
 };
 
 namespace qv {
@@ -344,8 +355,26 @@ qv_status build(qv_batch *b, const qv_batch_item *items, size_t count, const qv_
     // persistent queue takes the rest
     std::vector<char> solo(count, 0);
     auto solo_k = [&](int n) { return fixed_k ? opts->tile_bits : tuned_tile_bits(n, b->dt, false); };
-    if (jit_ok)
-        for (size_t c = 0; c < count; ++c) solo[c] = items[c].state->n - solo_k(items[c].state->n) >= 12;
+    if (jit_ok) {
+        // members with the same gate structure share their compiled passes (the
+        // kernel cache is keyed by source), so they go to their own passes from
+        // 2^kSoloTileBits tiles on; a structure of its own only from 2^12 tiles,
+        // where compiling its passes pays off
+        std::map<std::vector<int32_t>, int> shape_count;
+        std::vector<std::vector<int32_t>> shape(count);
+        for (size_t c = 0; c < count; ++c) {
+            shape[c].push_back(items[c].state->n);
+            for (size_t k = 0; k < items[c].ngates; ++k) {
+                const qv_gate &x = items[c].gates[k];
+                shape[c].insert(shape[c].end(), {int32_t(x.kind), x.target, x.target2, x.ctrl});
+            }
+            ++shape_count[shape[c]];
+        }
+        for (size_t c = 0; c < count; ++c) {
+            const int tiles = items[c].state->n - solo_k(items[c].state->n);
+            solo[c] = tiles >= 12 || (tiles >= kSoloTileBits && shape_count[shape[c]] > 1);
+        }
+    }
     // qubit counts whose queued circuits all share one gate structure run in the
     // compiled persistent kernel, the others in the interpreting one
     std::map<int, bool> uniform;
@@ -579,6 +608,21 @@ qv_status build(qv_batch *b, const qv_batch_item *items, size_t count, const qv_
         QV_TRY(allow_smem(reinterpret_cast<const void *>(batch_pauli_kernel<R>), 200 * 1024));
     }
     QV_CUDA(cudaMallocHost(reinterpret_cast<void **>(&b->host), (count + 2) * sizeof(double)));
+    // solo circuits, largest first, round-robin over the side streams
+    std::stable_sort(b->solo.begin(), b->solo.end(), [&](const qv_batch::Solo &x, const qv_batch::Solo &y) {
+        return nq[size_t(x.circuit)] > nq[size_t(y.circuit)];
+    });
+    const size_t nside = std::min<size_t>(b->solo.size(), kSideStreams);
+    for (size_t j = 0; j < nside; ++j) {
+        cudaStream_t st = nullptr;
+        QV_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        b->side.push_back(st);
+    }
+    for (size_t j = 0; j < (nside ? nside + 1 : 0); ++j) {
+        cudaEvent_t ev = nullptr;
+        QV_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        b->side_ev.push_back(ev);
+    }
     // ---- capture the whole run in one graph
     QV_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t ce = cudaSuccess;
@@ -596,14 +640,26 @@ qv_status build(qv_batch *b, const qv_batch_item *items, size_t count, const qv_
                                                                                    int(count));
             ce = cudaGetLastError();
         }
+        // fork: the side streams start after the initialisation
+        if (ce == cudaSuccess && !b->side.empty()) {
+            ce = cudaEventRecord(b->side_ev[0], b->stream);
+            for (size_t j = 0; j < b->side.size() && ce == cudaSuccess; ++j)
+                ce = cudaStreamWaitEvent(b->side[j], b->side_ev[0], 0);
+        }
         for (size_t gi = 0; gi < b->groups.size() && ce == cudaSuccess; ++gi) {
             const bool ok = launch_group<R>(b, b->groups[gi], b->next + gi);
             ce = ok ? cudaGetLastError() : cudaErrorLaunchFailure;
         }
-        for (const auto &so : b->solo) {
+        for (size_t k = 0; k < b->solo.size(); ++k) {
             if (ce != cudaSuccess) break;
-            const qv_status r = jit_launch(items[so.circuit].state, *so.prog, b->stream);
+            const auto &so = b->solo[k];
+            const qv_status r = jit_launch(items[so.circuit].state, *so.prog, b->side[k % b->side.size()]);
             ce = r == QV_OK ? cudaGetLastError() : cudaErrorLaunchFailure;
+        }
+        // join: the reduction and the copies wait for every side stream
+        for (size_t j = 0; j < b->side.size() && ce == cudaSuccess; ++j) {
+            ce = cudaEventRecord(b->side_ev[j + 1], b->side[j]);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->stream, b->side_ev[j + 1], 0);
         }
         if (nt && ce == cudaSuccess) {
             batch_pauli_kernel<R><<<dim3(kBlocksPerState, unsigned(count)), kBThreads,
@@ -638,6 +694,8 @@ void batch_release(qv_batch *b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     for (void *p : b->owned) cudaFree(p);
+    for (cudaEvent_t ev : b->side_ev) cudaEventDestroy(ev);
+    for (cudaStream_t st : b->side) cudaStreamDestroy(st);
     if (b->host) cudaFreeHost(b->host);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;

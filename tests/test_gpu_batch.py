@@ -207,3 +207,38 @@ def test_batch_large_member_runs_its_own_passes(qvlib, orc, cuda):
     finally:
         for h in states:
             qv.qv_destroy(h)
+
+
+def test_batch_members_on_side_streams(qvlib, orc, cuda):
+    """Members whose passes have at least 2^8 tiles run on their own compiled
+    passes, spread over the batch graph's side streams: twenty parameter sets of
+    a 19-qubit ansatz (2^8 tiles of 2^11 amplitudes per pass). Energies equal
+    the oracle's on sampled sets and the one-by-one GPU path on all of them,
+    over two replays."""
+    qv = qvlib
+    n, layers, count = 19, 3, 20
+    terms = W.ansatz_hamiltonian(n)
+    circuits = [W.ansatz_circuit(n, layers, W.config_seed(2, 500 + c))[0] for c in range(count)]
+    states = [qv.qv_create(n, 0) for _ in range(count)]
+    try:
+        b = qv.Batch(list(zip(states, circuits)), terms, tile_bits=11)
+        info = b.info()
+        assert len(info) == count and all(g["compiled"] == 2 and g["qubits"] == n for g in info)
+        h = qv.qv_create(n, 0)
+        one = []
+        for c in range(count):
+            qv.qv_set_basis(h, 0)
+            qv.qv_apply_circuit(h, circuits[c], tile_bits=11)
+            one.append(qv.qv_expect_pauli(h, terms))
+        qv.qv_destroy(h)
+        for rep in range(2):
+            e = b.run()
+            for c in (0, 7, count - 1):
+                assert e[c] == pytest.approx(orc.energy(n, circuits[c], terms), abs=2e-5), (c, rep)
+            assert np.max(np.abs(np.array(e) - np.array(one))) <= 2e-5, rep
+        psi = qv.qv_get_state(states[count - 1])
+        assert np.linalg.norm(psi.astype(complex) - orc.run(n, circuits[count - 1])) <= 1e-5
+        b.close()
+    finally:
+        for h in states:
+            qv.qv_destroy(h)
