@@ -130,6 +130,12 @@ QI void cm2(u64 dr, u64 di, u64 dn, u64 &ar, u64 &ai) {
     ar = f2fma(dr, xr, f2mul(dn, xi));
     ai = f2fma(dr, xi, f2mul(di, xr));
 }
+// sign flips: amplitude v (both packed lanes, real and imaginary parts) XOR m[v]
+QI void xs8(u64 (&r)[8], u64 (&i)[8], u64 m0, u64 m1, u64 m2, u64 m3, u64 m4, u64 m5, u64 m6, u64 m7) {
+    const u64 m[8] = {m0, m1, m2, m3, m4, m5, m6, m7};
+#pragma unroll
+    for (int v = 0; v < 8; ++v) { r[v] ^= m[v]; i[v] ^= m[v]; }
+}
 // scalar pair with the lane-0 values of c
 QI void ap1(const u64 (&c)[12], float &ar, float &ai, float &br, float &bi) {
     float u[8], t;
@@ -426,6 +432,40 @@ void emit_gen2_c64(std::ostream &o, const plan::Op &op, int O)
     }
 }
 
+// A diagonal op of +1 / -1 entries as sign-bit XORs (integer pipe, exact): the
+// mask of register v has bit 31 set where lane 0 is negated and bit 63 where
+// lane 1 is. Target bit b and select value s of each amplitude come from its
+// register index (bits 0-2), its lane (bit 3: packed qubit), or a runtime
+// expression (a thread bit or a qubit outside the tile).
+void emit_sign_c64(std::ostream &o, const plan::Op &op, const std::string &sel)
+{
+    const int J = op.treg, C = op.sreg;
+    const bool rs = C < 0 && (op.sthr || op.sext);  // runtime select
+    const bool rt = J < 0;                           // runtime target bit
+    const std::string t1 = rt ? "(((tid & " + hex32(op.tthr) + ") != 0u) | ((base & " + hex64(op.text) + ") != 0ull))"
+                              : "false";
+    auto mask = [&](int v, int s_rt, int b_rt) {
+        uint64_t m = 0;
+        for (int l = 0; l < 2; ++l) {
+            const int b = rt ? b_rt : J == 3 ? l : (v >> J) & 1;
+            const int s = C < 0 ? (rs ? s_rt : 0) : C == 3 ? l : (v >> C) & 1;
+            if (op.M[s][b ? 3 : 0].real() < 0) m |= uint64_t(1) << (l ? 63 : 31);
+        }
+        return m;
+    };
+    o << "    { const int s = " << (rs ? sel : std::string("0")) << "; const bool tb = " << t1 << "; (void)s; (void)tb;\n";
+    o << "      xs8(r, i";
+    for (int v = 0; v < 8; ++v) {
+        const uint64_t m00 = mask(v, 0, 0), m01 = mask(v, 0, 1), m10 = mask(v, 1, 0), m11 = mask(v, 1, 1);
+        o << ", ";
+        if (m00 == m01 && m00 == m10 && m00 == m11) o << hex64(m00);
+        else
+            o << "(s ? (tb ? " << hex64(m11) << " : " << hex64(m10) << ") : (tb ? " << hex64(m01) << " : "
+              << hex64(m00) << "))";
+    }
+    o << ");\n    }\n";
+}
+
 void emit_op_c64(std::ostream &o, const plan::Op &op, int O)
 {
     if (op.type == plan::OP_GEN2) {
@@ -453,6 +493,8 @@ void emit_op_c64(std::ostream &o, const plan::Op &op, int O)
     } else if (op.type == plan::OP_X) {
         if (C < 0 && us && op.m0id) o << "    if (" << sel << ") x_op<" << J << ", -1>(r, i);\n";
         else o << "    x_op<" << J << ", " << C << ">(r, i);\n";
+    } else if (plan::sign_only(op)) {
+        emit_sign_c64(o, op, sel);
     } else {
         const int Jd = J >= 0 ? J : 4;
         const std::string t1 = Jd == 4 ? "(((tid & " + hex32(op.tthr) + ") != 0u) | ((base & " + hex64(op.text) +

@@ -994,7 +994,10 @@ bool make_plan(int n, int k, bool pin0, bool fuse, bool pairs, const std::vector
         stats.gates += P.ngates;
         stats.ops += int(P.ops.size());
         for (const Op &op : P.ops) {
-            const double f = op.type == OP_GEN ? 14.0 : op.type == OP_DIAG ? 6.0 : op.type == OP_GEN2 ? 30.0 : 0.0;
+            const double f = op.type == OP_GEN    ? 14.0
+                             : op.type == OP_DIAG ? (sign_only(op) ? 0.0 : 6.0)
+                             : op.type == OP_GEN2 ? 30.0
+                                                  : 0.0;
             stats.flops_per_amp += op.m0id ? 0.5 * f : f;
         }
         out.push_back(std::move(P));

@@ -79,6 +79,20 @@ struct Op {
     int gen = 0;                    // adjoint plans: generator form of the derivative (see PGate)
 };
 
+// A diagonal op whose entries are all +1 or -1 (Z, CZ and products of them):
+// it only flips signs, so the compiled engine applies it with sign-bit XORs
+// and the cost model counts no floating-point operations for it.
+inline bool sign_only(const Op &op)
+{
+    if (op.type != OP_DIAG) return false;
+    for (int s = 0; s < 2; ++s)
+        for (int e : {0, 3}) {
+            const std::complex<double> d = op.M[s][e];
+            if (d.imag() != 0.0 || (d.real() != 1.0 && d.real() != -1.0)) return false;
+        }
+    return true;
+}
+
 struct Layout {
     int8_t P[kRegBits];          // register bit j -> tile position
     int8_t Q[kMaxK - kRegBits];  // thread bit b -> tile position (lanes are b < 5)

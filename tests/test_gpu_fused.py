@@ -253,3 +253,27 @@ def test_permutation_passes_24q(qvlib, orc, cuda, k):
         assert dist(qv.qv_get_state(h), want) <= 1e-6
     finally:
         qv.qv_destroy(h)
+
+
+@pytest.mark.parametrize("n,k", [(11, 10), (14, 11), (20, 12)])
+def test_sign_flip_ops(qvlib, orc, cuda, n, k):
+    """Diagonal ops of +1 / -1 entries (Z, CZ) run as sign-bit flips: Z and CZ
+    on every kind of target and control position (register bits, the packed
+    lane qubit 0, thread bits, qubits outside the tile), between layers of
+    random rotations, on a random state; the result equals the oracle's."""
+    qv = qvlib
+    rot = W.random_gate_list(n, 2 * n, seed=300 + n, kinds=("u3", "ry", "h"), ctrl_prob=0.0)
+    signs = []
+    for q in range(n):
+        signs.append(Gate("z", q))
+        for c in (0, (q + 1) % n, (q + n // 2) % n, n - 1):
+            if c != q:
+                signs.append(Gate("z", q, ctrl=c))
+    gates = rot + signs + rot[::-1] + signs[::3] + W.random_gate_list(n, n, seed=700 + n, kinds=("u3",))
+    psi = W.random_state(n, 50 + n)
+    got = run_gpu(qv, n, 0, gates, psi=psi, tile_bits=k)
+    want = orc.run(n, gates, psi.copy())
+    assert dist(got, want) <= TOL[0]
+    # the same circuit through the per-gate kernels
+    plain = run_gpu(qv, n, 0, gates, psi=psi, mode=1)
+    assert dist(got, plain) <= TOL[0]

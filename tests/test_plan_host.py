@@ -32,7 +32,8 @@ def test_single_gate_cost(qv, dtype, ab):
 def test_op_kinds_cost(qv):
     n, N = 12, 1 << 12
     assert cost(qv, n, [Gate("x", 3, ctrl=0)], tile_bits=10)["flops"] == 0          # CNOT: a permutation
-    assert cost(qv, n, [Gate("z", 3, ctrl=0)], tile_bits=10)["flops"] == 3 * N      # CZ: diagonal, half the amps
+    assert cost(qv, n, [Gate("z", 3, ctrl=0)], tile_bits=10)["flops"] == 0          # CZ: sign flips only
+    assert cost(qv, n, [Gate("p", 3, ctrl=0, theta=(0.5, 0, 0))], tile_bits=10)["flops"] == 3 * N  # CP: diagonal, half
     assert cost(qv, n, [Gate("rz", 5, theta=(0.7, 0, 0))], tile_bits=10)["flops"] == 6 * N
     assert cost(qv, n, [Gate("u3", 4, ctrl=1, theta=(0.3, 0.2, 0.1))], tile_bits=10)["flops"] == 7 * N
 
