@@ -78,12 +78,11 @@ __global__ void __launch_bounds__(kThreads) pauli_apply_kernel(const R *__restri
             } else {
                 zsign_sum<R>(src, g[q].z, g[q].cre, g[q].cim, g[q].nt, g[q].has_im != 0, cr, ci);
             }
-            const R vr = psi[2 * src], vi = psi[2 * src + 1];
-            ar += cr * vr - ci * vi;
-            ai += cr * vi + ci * vr;
+            const auto v = load_amp(psi, src);
+            ar += cr * v.x - ci * v.y;
+            ai += cr * v.y + ci * v.x;
         }
-        out[2 * j] = ar;
-        out[2 * j + 1] = ai;
+        reinterpret_cast<typename Cplx<R>::V *>(out)[j] = {ar, ai};
     }
 }
 

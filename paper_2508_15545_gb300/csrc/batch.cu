@@ -172,30 +172,8 @@ __global__ void __launch_bounds__(kBThreads) batch_pauli_kernel(R *const *amps, 
     const uint64_t per = (N + kBlocksPerState - 1) / kBlocksPerState;
     const uint64_t i0 = uint64_t(blockIdx.x) * per, i1 = min(N, i0 + per);
     CompSum<R> acc;
-    for (uint64_t i = i0 + threadIdx.x; i < i1; i += kBThreads) {
-        const R ar = a[2 * i], ai = a[2 * i + 1];
-#pragma unroll 4  // lets the partner loads of several groups be in flight together
-        for (int q = 0; q < ng; ++q) {
-            const uint64_t j = i ^ g[q].x;
-            const R br = a[2 * j], bi = a[2 * j + 1];
-            const R pr = br * ar + bi * ai, pi = br * ai - bi * ar;  // conj(b) a
-            R cr, ci;
-            if (g[q].zero_z) {
-                if constexpr (sizeof(R) == 4) {
-                    cr = g[q].f0re;
-                    ci = g[q].f0im;
-                } else {
-                    cr = g[q].c0re;
-                    ci = g[q].c0im;
-                }
-            } else if constexpr (sizeof(R) == 4) {
-                zsign_sum<R>(i, g[q].z, g[q].fre, g[q].fim, g[q].nt, g[q].has_im != 0, cr, ci);
-            } else {
-                zsign_sum<R>(i, g[q].z, g[q].cre, g[q].cim, g[q].nt, g[q].has_im != 0, cr, ci);
-            }
-            acc.add(pr * cr - pi * ci);
-        }
-    }
+    // per amplitude a plain sum over the groups, across amplitudes with compensation
+    for (uint64_t i = i0 + threadIdx.x; i < i1; i += kBThreads) acc.add(pauli_amp_sum<R>(a, i, g, ng));
     double v = acc.value();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -160,6 +160,47 @@ __device__ __forceinline__ void exact_norm2(double re, double im, double &h, dou
 
 // Running compensated sum in precision R: hi + lo carries the exact sum of
 // everything added so far up to the rounding of lo.
+// One complex amplitude (re, im) as one 8-byte (complex64) or 16-byte
+// (complex128) load.
+template <typename R> struct Cplx;
+template <> struct Cplx<float> { using V = float2; };
+template <> struct Cplx<double> { using V = double2; };
+template <typename R> __device__ __forceinline__ typename Cplx<R>::V load_amp(const R *amp, uint64_t i)
+{
+    return reinterpret_cast<const typename Cplx<R>::V *>(amp)[i];
+}
+
+// Sum over the X-mask groups of Re( conj(a_{i^x}) c(i) a_i ) for amplitude i
+// (a group has x, zero_z, has_im, nt, z, the coefficients c0re/c0im, cre/cim in
+// double and f0re/f0im, fre/fim in float), in the state's precision.
+template <typename R, typename G>
+__device__ __forceinline__ R pauli_amp_sum(const R *__restrict__ amp, uint64_t i, const G *g, int ng)
+{
+    const auto a = load_amp(amp, i);
+    R s = 0;
+#pragma unroll 4  // lets the partner loads of several groups be in flight together
+    for (int q = 0; q < ng; ++q) {
+        const auto b = g[q].x ? load_amp(amp, i ^ g[q].x) : a;
+        const R pr = b.x * a.x + b.y * a.y, pi = b.x * a.y - b.y * a.x;  // conj(b) a
+        R cr, ci;
+        if (g[q].zero_z) {
+            if constexpr (sizeof(R) == 4) {
+                cr = g[q].f0re;
+                ci = g[q].f0im;
+            } else {
+                cr = g[q].c0re;
+                ci = g[q].c0im;
+            }
+        } else if constexpr (sizeof(R) == 4) {
+            zsign_sum<R>(i, g[q].z, g[q].fre, g[q].fim, g[q].nt, g[q].has_im != 0, cr, ci);
+        } else {
+            zsign_sum<R>(i, g[q].z, g[q].cre, g[q].cim, g[q].nt, g[q].has_im != 0, cr, ci);
+        }
+        s += pr * cr - pi * ci;
+    }
+    return s;
+}
+
 template <typename R> struct CompSum {
     R hi = 0, lo = 0;
     __device__ __forceinline__ void add(R x)

@@ -255,28 +255,9 @@ __global__ void __launch_bounds__(kThreads) pauli_all_kernel(const R *__restrict
     __syncthreads();
     CompSum<R> acc;
     for (uint64_t i = uint64_t(blockIdx.x) * kThreads + threadIdx.x; i < N; i += uint64_t(gridDim.x) * kThreads) {
-        const R ar = amp[2 * i], ai = amp[2 * i + 1];
-#pragma unroll 4  // lets the partner loads of several groups be in flight together
-        for (int q = 0; q < ng; ++q) {
-            const uint64_t j = i ^ g[q].x;
-            const R br = amp[2 * j], bi = amp[2 * j + 1];
-            const R pr = br * ar + bi * ai, pi = br * ai - bi * ar;  // conj(b) a
-            R cr, ci;
-            if (g[q].zero_z) {
-                if constexpr (sizeof(R) == 4) {
-                    cr = g[q].f0re;
-                    ci = g[q].f0im;
-                } else {
-                    cr = g[q].c0re;
-                    ci = g[q].c0im;
-                }
-            } else if constexpr (sizeof(R) == 4) {
-                zsign_sum<R>(i, g[q].z, g[q].fre, g[q].fim, g[q].nt, g[q].has_im != 0, cr, ci);
-            } else {
-                zsign_sum<R>(i, g[q].z, g[q].cre, g[q].cim, g[q].nt, g[q].has_im != 0, cr, ci);
-            }
-            acc.add(pr * cr - pi * ci);
-        }
+        // the terms of one amplitude are summed plainly (a few dozen of similar
+        // size); the amplitudes' sums are added with compensation
+        acc.add(pauli_amp_sum<R>(amp, i, g, ng));
     }
     double x[1] = {acc.value()};
     block_sum<1>(x, smem);
