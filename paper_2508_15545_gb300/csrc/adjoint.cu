@@ -68,19 +68,28 @@ __global__ void __launch_bounds__(kThreads) pauli_apply_kernel(const R *__restri
     __syncthreads();
     for (uint64_t j = uint64_t(blockIdx.x) * kThreads + threadIdx.x; j < N; j += uint64_t(gridDim.x) * kThreads) {
         R ar = 0, ai = 0;
-#pragma unroll 4  // lets the partner loads of several groups be in flight together
-        for (int q = 0; q < ng; ++q) {
-            const uint64_t src = j ^ g[q].x;
-            R cr, ci;
-            if (g[q].zero_z) {
-                cr = g[q].c0re;
-                ci = g[q].c0im;
-            } else {
-                zsign_sum<R>(src, g[q].z, g[q].cre, g[q].cim, g[q].nt, g[q].has_im != 0, cr, ci);
+        // the partner loads of eight groups are issued before any is used (the far
+        // partners come from DRAM; the kernel is bound by their latency)
+        for (int q0 = 0; q0 < ng; q0 += 8) {
+            typename Cplx<R>::V v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (q0 + u < ng) v[u] = load_amp(psi, j ^ g[q0 + u].x);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int q = q0 + u;
+                if (q >= ng) break;
+                const uint64_t src = j ^ g[q].x;
+                R cr, ci;
+                if (g[q].zero_z) {
+                    cr = g[q].c0re;
+                    ci = g[q].c0im;
+                } else {
+                    zsign_sum<R>(src, g[q].z, g[q].cre, g[q].cim, g[q].nt, g[q].has_im != 0, cr, ci);
+                }
+                ar += cr * v[u].x - ci * v[u].y;
+                ai += cr * v[u].y + ci * v[u].x;
             }
-            const auto v = load_amp(psi, src);
-            ar += cr * v.x - ci * v.y;
-            ai += cr * v.y + ci * v.x;
         }
         reinterpret_cast<typename Cplx<R>::V *>(out)[j] = {ar, ai};
     }

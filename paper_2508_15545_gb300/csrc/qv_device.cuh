@@ -176,27 +176,39 @@ template <typename R> __device__ __forceinline__ typename Cplx<R>::V load_amp(co
 template <typename R, typename G>
 __device__ __forceinline__ R pauli_amp_sum(const R *__restrict__ amp, uint64_t i, const G *g, int ng)
 {
-    const auto a = load_amp(amp, i);
+    using V = typename Cplx<R>::V;
+    const V a = load_amp(amp, i);
     R s = 0;
-#pragma unroll 4  // lets the partner loads of several groups be in flight together
-    for (int q = 0; q < ng; ++q) {
-        const auto b = g[q].x ? load_amp(amp, i ^ g[q].x) : a;
-        const R pr = b.x * a.x + b.y * a.y, pi = b.x * a.y - b.y * a.x;  // conj(b) a
-        R cr, ci;
-        if (g[q].zero_z) {
-            if constexpr (sizeof(R) == 4) {
-                cr = g[q].f0re;
-                ci = g[q].f0im;
-            } else {
-                cr = g[q].c0re;
-                ci = g[q].c0im;
-            }
-        } else if constexpr (sizeof(R) == 4) {
-            zsign_sum<R>(i, g[q].z, g[q].fre, g[q].fim, g[q].nt, g[q].has_im != 0, cr, ci);
-        } else {
-            zsign_sum<R>(i, g[q].z, g[q].cre, g[q].cim, g[q].nt, g[q].has_im != 0, cr, ci);
+    // the partner loads of eight groups are issued before any is used: the far
+    // partners come from DRAM, and the sum is bound by their latency
+    for (int q0 = 0; q0 < ng; q0 += 8) {
+        V b[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int q = q0 + u;
+            b[u] = (q < ng && g[q].x) ? load_amp(amp, i ^ g[q].x) : a;
         }
-        s += pr * cr - pi * ci;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int q = q0 + u;
+            if (q >= ng) break;
+            const R pr = b[u].x * a.x + b[u].y * a.y, pi = b[u].x * a.y - b[u].y * a.x;  // conj(b) a
+            R cr, ci;
+            if (g[q].zero_z) {
+                if constexpr (sizeof(R) == 4) {
+                    cr = g[q].f0re;
+                    ci = g[q].f0im;
+                } else {
+                    cr = g[q].c0re;
+                    ci = g[q].c0im;
+                }
+            } else if constexpr (sizeof(R) == 4) {
+                zsign_sum<R>(i, g[q].z, g[q].fre, g[q].fim, g[q].nt, g[q].has_im != 0, cr, ci);
+            } else {
+                zsign_sum<R>(i, g[q].z, g[q].cre, g[q].cim, g[q].nt, g[q].has_im != 0, cr, ci);
+            }
+            s += pr * cr - pi * ci;
+        }
     }
     return s;
 }
