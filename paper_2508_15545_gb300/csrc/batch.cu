@@ -172,8 +172,16 @@ __global__ void __launch_bounds__(kBThreads) batch_pauli_kernel(R *const *amps, 
     const uint64_t per = (N + kBlocksPerState - 1) / kBlocksPerState;
     const uint64_t i0 = uint64_t(blockIdx.x) * per, i1 = min(N, i0 + per);
     CompSum<R> acc;
-    // per amplitude a plain sum over the groups, across amplitudes with compensation
-    for (uint64_t i = i0 + threadIdx.x; i < i1; i += kBThreads) acc.add(pauli_amp_sum<R>(a, i, g, ng));
+    // per amplitude a plain sum over the groups, across amplitudes with compensation;
+    // four amplitudes a thread at a time (the group fields read once for the four)
+    uint64_t i = i0 + threadIdx.x;
+    for (; i + 3 * kBThreads < i1; i += 4 * kBThreads) {
+        R s4[4];
+        pauli_amp_sums<R, 4, 4>(a, i, kBThreads, g, ng, s4);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc.add(s4[k]);
+    }
+    for (; i < i1; i += kBThreads) acc.add(pauli_amp_sum<R>(a, i, g, ng));
     double v = acc.value();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

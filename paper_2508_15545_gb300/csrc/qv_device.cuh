@@ -213,6 +213,82 @@ __device__ __forceinline__ R pauli_amp_sum(const R *__restrict__ amp, uint64_t i
     return s;
 }
 
+// The same for NA amplitudes i0 + a * stride at once: each group's fields and
+// each Z term are read once for all of them, and the partner loads of QB
+// groups are issued before any is used. s[a] gets amplitude a's sum (a plain
+// sum in the state's precision).
+template <typename R, int NA, int QB, typename G>
+__device__ __forceinline__ void pauli_amp_sums(const R *__restrict__ amp, uint64_t i0, uint64_t stride, const G *g,
+                                               int ng, R (&s)[NA])
+{
+    using V = typename Cplx<R>::V;
+    V a[NA];
+#pragma unroll
+    for (int k = 0; k < NA; ++k) {
+        a[k] = load_amp(amp, i0 + k * stride);
+        s[k] = 0;
+    }
+    for (int q0 = 0; q0 < ng; q0 += QB) {
+        V b[QB][NA];
+#pragma unroll
+        for (int u = 0; u < QB; ++u) {
+            const int q = q0 + u;
+            const uint64_t x = q < ng ? g[q].x : 0;
+#pragma unroll
+            for (int k = 0; k < NA; ++k) b[u][k] = x ? load_amp(amp, (i0 + k * stride) ^ x) : a[k];
+        }
+#pragma unroll
+        for (int u = 0; u < QB; ++u) {
+            const int q = q0 + u;
+            if (q >= ng) break;
+            R cr[NA], ci[NA];
+            if (g[q].zero_z) {
+                R c0r, c0i;
+                if constexpr (sizeof(R) == 4) {
+                    c0r = g[q].f0re;
+                    c0i = g[q].f0im;
+                } else {
+                    c0r = g[q].c0re;
+                    c0i = g[q].c0im;
+                }
+#pragma unroll
+                for (int k = 0; k < NA; ++k) {
+                    cr[k] = c0r;
+                    ci[k] = c0i;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < NA; ++k) cr[k] = ci[k] = R(0);
+                const bool him = g[q].has_im != 0;
+                for (int t = 0; t < g[q].nt; ++t) {
+                    const uint64_t zk = g[q].z[t];
+                    R fr, fi;
+                    if constexpr (sizeof(R) == 4) {
+                        fr = g[q].fre[t];
+                        fi = g[q].fim[t];
+                    } else {
+                        fr = g[q].cre[t];
+                        fi = g[q].cim[t];
+                    }
+#pragma unroll
+                    for (int k = 0; k < NA; ++k) {
+                        const uint64_t i = i0 + k * stride;
+                        const uint32_t par = (__popc(uint32_t(i) & uint32_t(zk)) ^ __popc(uint32_t(i >> 32) & uint32_t(zk >> 32))) & 1u;
+                        const R sg = par ? R(-1) : R(1);
+                        cr[k] += sg * fr;
+                        if (him) ci[k] += sg * fi;
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NA; ++k) {
+                const R pr = b[u][k].x * a[k].x + b[u][k].y * a[k].y, pi = b[u][k].x * a[k].y - b[u][k].y * a[k].x;
+                s[k] += pr * cr[k] - pi * ci[k];
+            }
+        }
+    }
+}
+
 template <typename R> struct CompSum {
     R hi = 0, lo = 0;
     __device__ __forceinline__ void add(R x)

@@ -254,11 +254,19 @@ __global__ void __launch_bounds__(kThreads) pauli_all_kernel(const R *__restrict
         reinterpret_cast<uint64_t *>(g)[k] = reinterpret_cast<const uint64_t *>(groups)[k];
     __syncthreads();
     CompSum<R> acc;
-    for (uint64_t i = uint64_t(blockIdx.x) * kThreads + threadIdx.x; i < N; i += uint64_t(gridDim.x) * kThreads) {
-        // the terms of one amplitude are summed plainly (a few dozen of similar
-        // size); the amplitudes' sums are added with compensation
-        acc.add(pauli_amp_sum<R>(amp, i, g, ng));
+    // the terms of one amplitude are summed plainly (a few dozen of similar size);
+    // the amplitudes' sums are added with compensation. Four amplitudes a thread
+    // at a time: the group fields are read once for the four, and more partner
+    // loads are in flight.
+    const uint64_t S = uint64_t(gridDim.x) * kThreads;
+    uint64_t i = uint64_t(blockIdx.x) * kThreads + threadIdx.x;
+    for (; i + 3 * S < N; i += 4 * S) {
+        R s4[4];
+        pauli_amp_sums<R, 4, 4>(amp, i, S, g, ng, s4);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc.add(s4[k]);
     }
+    for (; i < N; i += S) acc.add(pauli_amp_sum<R>(amp, i, g, ng));
     double x[1] = {acc.value()};
     block_sum<1>(x, smem);
     if (threadIdx.x == 0) part[blockIdx.x] = x[0];
