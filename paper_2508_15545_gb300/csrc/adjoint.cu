@@ -11,6 +11,7 @@
 // (Jones and Gacon, "Efficient calculation of gradients in classical
 // simulations of variational quantum algorithms", arXiv:2009.02823).
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -66,33 +67,63 @@ __global__ void __launch_bounds__(kThreads) pauli_apply_kernel(const R *__restri
     for (int k = threadIdx.x; k < ng * int(sizeof(PauliGroupA<R>) / 8); k += kThreads)
         reinterpret_cast<uint64_t *>(g)[k] = reinterpret_cast<const uint64_t *>(groups)[k];
     __syncthreads();
-    for (uint64_t j = uint64_t(blockIdx.x) * kThreads + threadIdx.x; j < N; j += uint64_t(gridDim.x) * kThreads) {
-        R ar = 0, ai = 0;
-        // the partner loads of eight groups are issued before any is used (the far
-        // partners come from DRAM; the kernel is bound by their latency)
-        for (int q0 = 0; q0 < ng; q0 += 8) {
-            typename Cplx<R>::V v[8];
+    // NA outputs j0 + k * S a thread at a time: each group's fields and Z terms are
+    // read once for them, and the partner loads of four groups for all of them are
+    // issued before any is used (the far partners come from DRAM; the kernel is
+    // bound by their latency)
+    using V = typename Cplx<R>::V;
+    const uint64_t S = uint64_t(gridDim.x) * kThreads;
+    uint64_t j0 = uint64_t(blockIdx.x) * kThreads + threadIdx.x;
+    auto outputs = [&](auto na) {
+        constexpr int NA = decltype(na)::value;
+        R ar[NA], ai[NA];
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (q0 + u < ng) v[u] = load_amp(psi, j ^ g[q0 + u].x);
+        for (int k = 0; k < NA; ++k) ar[k] = ai[k] = R(0);
+        for (int q0 = 0; q0 < ng; q0 += 4) {
+            V v[4][NA];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int k = 0; k < NA; ++k)
+                    if (q0 + u < ng) v[u][k] = load_amp(psi, (j0 + k * S) ^ g[q0 + u].x);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
                 const int q = q0 + u;
                 if (q >= ng) break;
-                const uint64_t src = j ^ g[q].x;
-                R cr, ci;
-                if (g[q].zero_z) {
-                    cr = g[q].c0re;
-                    ci = g[q].c0im;
-                } else {
-                    zsign_sum<R>(src, g[q].z, g[q].cre, g[q].cim, g[q].nt, g[q].has_im != 0, cr, ci);
+                R cr[NA], ci[NA];
+#pragma unroll
+                for (int k = 0; k < NA; ++k) {
+                    cr[k] = g[q].zero_z ? g[q].c0re : R(0);
+                    ci[k] = g[q].zero_z ? g[q].c0im : R(0);
                 }
-                ar += cr * v[u].x - ci * v[u].y;
-                ai += cr * v[u].y + ci * v[u].x;
+                if (!g[q].zero_z) {
+                    const bool him = g[q].has_im != 0;
+                    for (int t = 0; t < g[q].nt; ++t) {
+                        const uint64_t zk = g[q].z[t];
+                        const R fr = g[q].cre[t], fi = g[q].cim[t];
+#pragma unroll
+                        for (int k = 0; k < NA; ++k) {
+                            const uint64_t src = (j0 + k * S) ^ g[q].x;
+                            const uint32_t par =
+                                (__popc(uint32_t(src) & uint32_t(zk)) ^ __popc(uint32_t(src >> 32) & uint32_t(zk >> 32))) & 1u;
+                            const R sg = par ? R(-1) : R(1);
+                            cr[k] += sg * fr;
+                            if (him) ci[k] += sg * fi;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < NA; ++k) {
+                    ar[k] += cr[k] * v[u][k].x - ci[k] * v[u][k].y;
+                    ai[k] += cr[k] * v[u][k].y + ci[k] * v[u][k].x;
+                }
             }
         }
-        reinterpret_cast<typename Cplx<R>::V *>(out)[j] = {ar, ai};
-    }
+#pragma unroll
+        for (int k = 0; k < NA; ++k) reinterpret_cast<V *>(out)[j0 + k * S] = V{ar[k], ai[k]};
+    };
+    for (; j0 + 3 * S < N; j0 += 4 * S) outputs(std::integral_constant<int, 4>{});
+    for (; j0 < N; j0 += S) outputs(std::integral_constant<int, 1>{});
 }
 
 // ---------------------------------------------------------------- Re <a|b>
