@@ -116,6 +116,11 @@ QI u64 pk(float lo, float hi) { u64 r; asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "
 QI void upk(u64 v, float &lo, float &hi) { asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v)); }
 QI u64 f2fma(u64 a, u64 b, u64 c) { u64 d; asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c)); return d; }
 QI u64 f2mul(u64 a, u64 b) { u64 d; asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b)); return d; }
+// asynchronous 16-byte copy global -> shared (through L2 only), and waiting for this thread's copies
+QI u32 sh_addr(const void *p) { return (u32)__cvta_generic_to_shared(p); }
+QI void cp16(u32 dst, const void *src) { asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(dst), "l"(src) : "memory"); }
+QI void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+QI void cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // complex64: (a, b) <- U (a, b) on two packed pairs; c = (re, im, -im) pairs of U00 U01 U10 U11
 QI void ap2(const u64 (&c)[12], u64 &ar, u64 &ai, u64 &br, u64 &bi) {
@@ -1250,7 +1255,10 @@ std::string gen_source_adj(const plan::Pass &p, int nslots)
       << ") qv_adj(float *__restrict__ amp, float *__restrict__ lam, u64 ntiles, double *part, int Gc, "
          "const QvAdjArgs cf)\n{\n";
     o << "    extern __shared__ __align__(16) u64 sm[];\n";
-    o << "    float *sacc = reinterpret_cast<float *>(sm + " << (size_t(1) << p.k) << ");\n";
+    // shared memory: 2^k transpose words, then the next tile of psi and of lambda
+    // (thread tid's eight 16-byte words at word v * T + tid of each, copied
+    // asynchronously while the current tile computes), then the accumulators
+    o << "    float *sacc = reinterpret_cast<float *>(sm + " << (size_t(3) << p.k) << ");\n";
     o << "    const u32 tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;\n";
     o << "    for (int q = tid; q < " << 2 * nslots * (T / 32) << "; q += " << T << ") sacc[q] = 0.f;\n";
     o << "    __syncthreads();\n";
@@ -1271,30 +1279,47 @@ std::string gen_source_adj(const plan::Pass &p, int nslots)
         o << "    const u32 wW" << s << " = " << thread_expr(word_mask(p.stages[s - 1].out.Q), false) << ";\n";
         o << "    const u32 wR" << s << " = " << thread_expr(word_mask(p.stages[s].in.Q), false) << ";\n";
     }
-    o << "    for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {\n";
-    o << "    const u64 base = 0ull";
-    for (int s = 0; s < p.nseg; ++s)
-        o << " | (((t >> " << p.seg_src[s] << ") & " << hex64((uint64_t(1) << p.seg_w[s]) - 1) << ") << "
-          << p.seg_dst[s] << ")";
-    o << ";\n";
     auto reg_offset = [&](const int8_t *P, int v) {
         uint32_t l = 0;
         for (int j = 0; j < 3; ++j)
             if ((v >> j) & 1) l |= 1u << P[j];
         return l;
     };
+    // copies of tile `tile` of psi and lambda into the prefetch buffers (if it exists)
+    auto issue = [&](const std::string &tile, const std::string &ind) {
+        o << ind << "if (" << tile << " < ntiles) { const u64 bn = " << tile_base_expr(p, tile) << ";\n";
+        for (int b = 0; b < 2; ++b) {
+            o << ind << "  { const float *a = " << (b ? "lam" : "amp") << " + 2 * (bn + gL); const u32 d = sh_addr(sm + "
+              << ((b + 1) << p.k) << ") + 16u * tid;\n";
+            for (int v = 0; v < 8; ++v)
+                o << ind << "    cp16(d + " << 16 * v * T << "u, a + 2 * " << hex64(G.phys(reg_offset(s0.in.P, v))) << ");\n";
+            o << ind << "  }\n";
+        }
+        o << ind << "}\n" << ind << "cp_commit();\n";
+    };
+    issue("(u64)blockIdx.x", "    ");
+    o << "    for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {\n";
+    o << "    const u64 base = 0ull";
+    for (int s = 0; s < p.nseg; ++s)
+        o << " | (((t >> " << p.seg_src[s] << ") & " << hex64((uint64_t(1) << p.seg_w[s]) - 1) << ") << "
+          << p.seg_dst[s] << ")";
+    o << ";\n";
     o << "    u64 r[8], i[8], rl[8], il[8];\n";
+    o << "    cp_wait_all();\n";
     for (int b = 0; b < 2; ++b) {
-        const char *src = b ? "lam" : "amp";
         const char *R = b ? "rl" : "r", *I = b ? "il" : "i";
-        o << "    { const float *a = " << src << " + 2 * (base + gL);\n";
+        o << "    { const float4 *pf = reinterpret_cast<const float4 *>(sm + " << ((b + 1) << p.k) << ") + tid;\n";
         for (int v = 0; v < 8; ++v)
-            o << "      const float4 f" << v << " = *reinterpret_cast<const float4 *>(a + 2 * "
-              << hex64(G.phys(reg_offset(s0.in.P, v))) << ");\n";
-        for (int v = 0; v < 8; ++v)
-            o << "      " << R << "[" << v << "] = pk(f" << v << ".x, f" << v << ".z); " << I << "[" << v << "] = pk(f" << v
-              << ".y, f" << v << ".w);\n";
+            o << "      { const float4 f = pf[" << v * T << "]; " << R << "[" << v << "] = pk(f.x, f.z); " << I << "["
+              << v << "] = pk(f.y, f.w); }\n";
         o << "    }\n";
+    }
+    // the next tile's copies go out once every thread has read its words of this
+    // one: after the first block barrier of the tile (added when the pass has no
+    // transpose)
+    if (p.stages.size() == 1) {
+        o << "    __syncthreads();\n";
+        issue("(t + gridDim.x)", "    ");
     }
     for (size_t s = 0; s < p.stages.size(); ++s) {
         const plan::Stage &st = p.stages[s];
@@ -1308,6 +1333,7 @@ std::string gen_source_adj(const plan::Pass &p, int nslots)
                   << "] = i[" << v << "];\n";
             }
             o << "      __syncthreads();\n";
+            if (s == 1) issue("(t + gridDim.x)", "      ");
             for (int v = 0; v < 8; ++v) {
                 const uint32_t w = swz8(reg_offset(st.in.P, v) >> 1);
                 o << "      r[" << v << "] = pre[wR" << s << " ^ " << hex32(w) << "]; i[" << v << "] = pim[wR" << s
@@ -1696,7 +1722,7 @@ qv_status jit_prepare_adjoint(qv_state *s, const std::vector<plan::Pass> &passes
         for (const plan::Op &op : passes[i].ops) nslots[i] += op.nd;
         srcs[i] = gen_source_adj(passes[i], nslots[i]);
         P->threads[i] = 1 << (passes[i].k - kRegBits);
-        smem[i] = 8 * (size_t(1) << passes[i].k) + size_t(2 * sizeof(float)) * nslots[i] * (P->threads[i] / 32);
+        smem[i] = 24 * (size_t(1) << passes[i].k) + size_t(2 * sizeof(float)) * nslots[i] * (P->threads[i] / 32);
         P->ntiles.push_back(dim(s) >> passes[i].k);
     }
     QV_TRY(get_kernels(s, srcs, "qv_adj", smem, P->threads, P->fns));
