@@ -50,7 +50,7 @@ template <typename R> struct PauliGroupA {
     int32_t nt;
     int32_t zero_z;       // every z mask is 0: c is the constant (c0re, c0im)
     int32_t has_im;       // some coefficient has an imaginary part
-    int32_t pad;
+    int32_t tab;          // chunks of Z-term tables (pure-Z group), 0: none
     R c0re, c0im;
     uint64_t z[kMaxTerms];
     R cre[kMaxTerms], cim[kMaxTerms];
@@ -59,13 +59,16 @@ template <typename R> struct PauliGroupA {
 // out_j = sum over groups sum_t c_t i^{ny_t} (-1)^{popcount(src & z_t)} psi_src, src = j ^ x
 template <typename R>
 __global__ void __launch_bounds__(kThreads) pauli_apply_kernel(const R *__restrict__ psi, R *__restrict__ out,
-                                                               uint64_t N, const PauliGroupA<R> *groups, int ng)
+                                                               uint64_t N, const PauliGroupA<R> *groups, int ng,
+                                                               const R *ztab, int tab_words)
 {
     extern __shared__ unsigned char smem_raw[];
     PauliGroupA<R> *g = reinterpret_cast<PauliGroupA<R> *>(smem_raw);
+    R *tab = reinterpret_cast<R *>(smem_raw + size_t(ng) * sizeof(PauliGroupA<R>));
     static_assert(sizeof(PauliGroupA<R>) % 8 == 0, "copied as 8-byte words");
     for (int k = threadIdx.x; k < ng * int(sizeof(PauliGroupA<R>) / 8); k += kThreads)
         reinterpret_cast<uint64_t *>(g)[k] = reinterpret_cast<const uint64_t *>(groups)[k];
+    for (int k = threadIdx.x; k < tab_words; k += kThreads) tab[k] = ztab[k];
     __syncthreads();
     // NA outputs j0 + k * S a thread at a time: each group's fields and Z terms are
     // read once for them, and the partner loads of four groups for all of them are
@@ -110,6 +113,10 @@ __global__ void __launch_bounds__(kThreads) pauli_apply_kernel(const R *__restri
                             cr[k] += sg * fr;
                             if (him) ci[k] += sg * fi;
                         }
+                    }
+                    if (g[q].tab) {
+#pragma unroll
+                        for (int k = 0; k < NA; ++k) ztab_add(tab, g[q].tab, (j0 + k * S) ^ g[q].x, him, cr[k], ci[k]);
                     }
                 }
 #pragma unroll
@@ -340,16 +347,21 @@ qv_status pauli_apply_impl(qv_state *s, const void *src, void *dst, const qv_pau
         gg.c0re = R(c0r);
         gg.c0im = R(c0i);
     }
-    const size_t gbytes = groups.size() * sizeof(PauliGroupA<R>);
-    if (gbytes > 200 * 1024) return fail(QV_ERR_UNSUPPORTED, "Hamiltonian too large (%zu X-mask groups)", groups.size());
-    QV_TRY(ensure_scratch(s, std::max<size_t>(gbytes, 8)));
+    // the pure-Z group's terms that lie inside one 8-bit chunk of the index go into tables
+    const std::vector<R> htab = ztab_for_group<R>(s->n, groups);
+    const size_t gbytes = groups.size() * sizeof(PauliGroupA<R>), tbytes = htab.size() * sizeof(R);
+    if (gbytes + tbytes > 200 * 1024)
+        return fail(QV_ERR_UNSUPPORTED, "Hamiltonian too large (%zu X-mask groups)", groups.size());
+    QV_TRY(ensure_scratch(s, std::max<size_t>(gbytes + tbytes, 8)));
     if (!groups.empty()) QV_TRY(copy_h2d(s, s->scratch.ptr, groups.data(), gbytes));
+    R *dtab = reinterpret_cast<R *>(static_cast<char *>(s->scratch.ptr) + gbytes);
+    if (tbytes) QV_TRY(copy_h2d(s, dtab, htab.data(), tbytes));
     QV_TRY(allow_smem(reinterpret_cast<const void *>(pauli_apply_kernel<R>), 200 * 1024));
     prof_bytes(s, QV_K_PAULI, double(dim(s)) * 2 * sizeof(R) * (2 + groups.size()));
     QV_LAUNCH(s, QV_K_PAULI,
-              pauli_apply_kernel<R><<<grid_of(s, dim(s)), kThreads, gbytes, s->stream>>>(
+              pauli_apply_kernel<R><<<grid_of(s, dim(s)), kThreads, gbytes + tbytes, s->stream>>>(
                   static_cast<const R *>(src), static_cast<R *>(dst), dim(s),
-                  static_cast<const PauliGroupA<R> *>(s->scratch.ptr), int(groups.size())));
+                  static_cast<const PauliGroupA<R> *>(s->scratch.ptr), int(groups.size()), dtab, int(htab.size())));
     return QV_OK;
 }
 

@@ -147,7 +147,7 @@ struct BGroup {
     int nt;
     int zero_z;   // every z mask is 0: c(i) is the constant (c0re, c0im)
     int has_im;   // some coefficient has an imaginary part
-    int pad;
+    int tab;      // chunks of Z-term tables (pure-Z group), 0: none
     double c0re, c0im;
     float f0re, f0im;
     uint64_t z[kMaxGroupTerms];
@@ -159,12 +159,14 @@ struct BGroup {
 // state of Re( conj(a_{i^x}) c(i) a_i ), summed over all X-mask groups.
 template <typename R>
 __global__ void __launch_bounds__(kBThreads) batch_pauli_kernel(R *const *amps, const int *nq, const BGroup *groups,
-                                                                int ng, double *part)
+                                                                int ng, const R *ztab, int tab_words, double *part)
 {
     extern __shared__ unsigned char sraw[];
     BGroup *g = reinterpret_cast<BGroup *>(sraw);
+    R *tab = reinterpret_cast<R *>(sraw + size_t(ng) * sizeof(BGroup));
     for (int k = threadIdx.x; k < ng * int(sizeof(BGroup) / 8); k += kBThreads)
         reinterpret_cast<uint64_t *>(g)[k] = reinterpret_cast<const uint64_t *>(groups)[k];
+    for (int k = threadIdx.x; k < tab_words; k += kBThreads) tab[k] = ztab[k];
     __syncthreads();
     const int c = blockIdx.y;
     const R *a = amps[c];
@@ -177,11 +179,11 @@ __global__ void __launch_bounds__(kBThreads) batch_pauli_kernel(R *const *amps, 
     uint64_t i = i0 + threadIdx.x;
     for (; i + 3 * kBThreads < i1; i += 4 * kBThreads) {
         R s4[4];
-        pauli_amp_sums<R, 4, 4>(a, i, kBThreads, g, ng, s4);
+        pauli_amp_sums<R, 4, 4>(a, i, kBThreads, g, ng, tab, s4);
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc.add(s4[k]);
     }
-    for (; i < i1; i += kBThreads) acc.add(pauli_amp_sum<R>(a, i, g, ng));
+    for (; i < i1; i += kBThreads) acc.add(pauli_amp_sum<R>(a, i, g, ng, tab));
     double v = acc.value();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -255,6 +257,8 @@ struct qv_batch {
     int *status = nullptr;                    // device status word
     void *hgroups = nullptr;                  // Pauli groups (device)
     int nhgroups = 0;
+    void *ztab = nullptr;                     // Z-term tables of the pure-Z group (device), or none
+    int ztab_words = 0;
     double *part = nullptr, *energies = nullptr;
     double *host = nullptr;                   // pinned: energies then status
     size_t nt = 0;
@@ -582,7 +586,22 @@ qv_status build(qv_batch *b, const qv_batch_item *items, size_t count, const qv_
                 gg.has_im |= gg.cim[k] != 0.0;
             }
         }
-        if (hg.size() * sizeof(BGroup) > 200 * 1024) return fail(QV_ERR_UNSUPPORTED, "Hamiltonian too large");
+        // the pure-Z group's terms that lie inside one 8-bit chunk of the index go into tables
+        int maxn = 0;
+        for (int v : nq) maxn = std::max(maxn, v);
+        const std::vector<R> htab = ztab_for_group<R>(maxn, hg);
+        for (BGroup &gg : hg)
+            for (int k = 0; k < gg.nt; ++k) {
+                gg.fre[k] = float(gg.cre[k]);
+                gg.fim[k] = float(gg.cim[k]);
+            }
+        if (hg.size() * sizeof(BGroup) + htab.size() * sizeof(R) > 200 * 1024)
+            return fail(QV_ERR_UNSUPPORTED, "Hamiltonian too large");
+        if (!htab.empty()) {
+            QV_TRY(dmalloc(b, &b->ztab, htab.size() * sizeof(R)));
+            QV_CUDA(cudaMemcpy(b->ztab, htab.data(), htab.size() * sizeof(R), cudaMemcpyHostToDevice));
+            b->ztab_words = int(htab.size());
+        }
         b->nhgroups = int(hg.size());
         QV_TRY(dmalloc(b, &b->hgroups, hg.size() * sizeof(BGroup)));
         QV_CUDA(cudaMemcpy(b->hgroups, hg.data(), hg.size() * sizeof(BGroup), cudaMemcpyHostToDevice));
@@ -649,9 +668,10 @@ qv_status build(qv_batch *b, const qv_batch_item *items, size_t count, const qv_
         }
         if (nt && ce == cudaSuccess) {
             batch_pauli_kernel<R><<<dim3(kBlocksPerState, unsigned(count)), kBThreads,
-                                    b->nhgroups * sizeof(BGroup), b->stream>>>(
+                                    b->nhgroups * sizeof(BGroup) + b->ztab_words * sizeof(R), b->stream>>>(
                 static_cast<R *const *>(b->amps), static_cast<const int *>(b->nq),
-                static_cast<const BGroup *>(b->hgroups), b->nhgroups, b->part);
+                static_cast<const BGroup *>(b->hgroups), b->nhgroups, static_cast<const R *>(b->ztab), b->ztab_words,
+                b->part);
             ce = cudaGetLastError();
             if (ce == cudaSuccess) {
                 batch_combine_kernel<<<unsigned((count + 127) / 128), 128, 0, b->stream>>>(b->part, int(count),

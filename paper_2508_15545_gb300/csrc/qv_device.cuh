@@ -1,6 +1,8 @@
 // Device-side helpers: index arithmetic and vectorised amplitude access.
 #pragma once
 
+#include <vector>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -170,11 +172,93 @@ template <typename R> __device__ __forceinline__ typename Cplx<R>::V load_amp(co
     return reinterpret_cast<const typename Cplx<R>::V *>(amp)[i];
 }
 
+// Tables of the Z terms of a pure-Z group (X mask 0). A term whose Z mask lies
+// inside one 8-bit chunk of the index (bits 8c .. 8c + 7) adds coef (-1)^popcount(v & m)
+// to entry v of chunk c's table (m: the mask shifted down by 8c); the group's
+// coefficient at index i is then the sum over chunks of entry (i >> 8c) & 255, plus
+// the terms that span two chunks, which the group keeps in its term list. Layout:
+// real parts at [c * 256 + v], imaginary parts at [(kZChunks + c) * 256 + v].
+constexpr int kZChunks = 5;  // indices up to 40 bits
+constexpr int kZTabWords = 2 * kZChunks * 256;
+
+// Host side: fills the tables (2 kZTabWords values, double) from the terms that fit a
+// chunk, moves the others to the front of z / cre / cim, and returns their count.
+// *nch gets the number of chunks that cover n qubits.
+inline int ztab_build(int n, uint64_t *z, double *cre, double *cim, int nt, double *tab, int *nch)
+{
+    const int nc = (n + 7) / 8;
+    for (int e = 0; e < kZTabWords; ++e) tab[e] = 0.0;
+    int keep = 0;
+    for (int k = 0; k < nt; ++k) {
+        int chunk = -1;
+        for (int c = 0; c < nc && chunk < 0; ++c)
+            if ((z[k] & ((uint64_t(1) << (8 * c)) - 1)) == 0 && (z[k] >> (8 * c)) < 256) chunk = c;
+        if (chunk < 0) {
+            z[keep] = z[k];
+            cre[keep] = cre[k];
+            cim[keep] = cim[k];
+            ++keep;
+            continue;
+        }
+        const unsigned m = unsigned(z[k] >> (8 * chunk));
+        for (unsigned v = 0; v < 256; ++v) {
+            const double sg = (__builtin_popcount(v & m) & 1) ? -1.0 : 1.0;
+            tab[chunk * 256 + v] += sg * cre[k];
+            tab[(kZChunks + chunk) * 256 + v] += sg * cim[k];
+        }
+    }
+    *nch = nc;
+    return keep;
+}
+
+// Host side, for a list of X-mask groups (fields x, zero_z, nt, z, cre, cim, tab): the
+// first pure-Z group with at least four terms that fit a chunk gets its tables
+// (returned in the state's precision, kZTabWords values) and keeps only its other
+// terms; returns an empty vector when no group qualifies. Callers refresh any
+// per-precision copies of the kept coefficients.
+template <typename R, typename G> std::vector<R> ztab_for_group(int n, std::vector<G> &groups)
+{
+    for (G &g : groups) {
+        if (g.x != 0 || g.zero_z || g.nt < 4) continue;
+        uint64_t z[64];
+        double cr[64], ci[64];
+        for (int k = 0; k < g.nt; ++k) {
+            z[k] = g.z[k];
+            cr[k] = double(g.cre[k]);
+            ci[k] = double(g.cim[k]);
+        }
+        std::vector<double> tab(kZTabWords);
+        int nch = 0;
+        const int keep = ztab_build(n, z, cr, ci, g.nt, tab.data(), &nch);
+        if (g.nt - keep < 4) return {};
+        for (int k = 0; k < keep; ++k) {
+            g.z[k] = z[k];
+            g.cre[k] = decltype(+g.cre[0])(cr[k]);
+            g.cim[k] = decltype(+g.cim[0])(ci[k]);
+        }
+        g.nt = keep;
+        g.tab = nch;
+        return std::vector<R>(tab.begin(), tab.end());
+    }
+    return {};
+}
+
+// Device side: adds the tables' entries for index i (nch chunks).
+template <typename R>
+__device__ __forceinline__ void ztab_add(const R *tab, int nch, uint64_t i, bool him, R &cr, R &ci)
+{
+    for (int c = 0; c < nch; ++c) {
+        const uint32_t v = uint32_t(i >> (8 * c)) & 255u;
+        cr += tab[c * 256 + v];
+        if (him) ci += tab[(kZChunks + c) * 256 + v];
+    }
+}
+
 // Sum over the X-mask groups of Re( conj(a_{i^x}) c(i) a_i ) for amplitude i
 // (a group has x, zero_z, has_im, nt, z, the coefficients c0re/c0im, cre/cim in
 // double and f0re/f0im, fre/fim in float), in the state's precision.
 template <typename R, typename G>
-__device__ __forceinline__ R pauli_amp_sum(const R *__restrict__ amp, uint64_t i, const G *g, int ng)
+__device__ __forceinline__ R pauli_amp_sum(const R *__restrict__ amp, uint64_t i, const G *g, int ng, const R *tab)
 {
     using V = typename Cplx<R>::V;
     const V a = load_amp(amp, i);
@@ -202,10 +286,10 @@ __device__ __forceinline__ R pauli_amp_sum(const R *__restrict__ amp, uint64_t i
                     cr = g[q].c0re;
                     ci = g[q].c0im;
                 }
-            } else if constexpr (sizeof(R) == 4) {
-                zsign_sum<R>(i, g[q].z, g[q].fre, g[q].fim, g[q].nt, g[q].has_im != 0, cr, ci);
             } else {
-                zsign_sum<R>(i, g[q].z, g[q].cre, g[q].cim, g[q].nt, g[q].has_im != 0, cr, ci);
+                if constexpr (sizeof(R) == 4) zsign_sum<R>(i, g[q].z, g[q].fre, g[q].fim, g[q].nt, g[q].has_im != 0, cr, ci);
+                else zsign_sum<R>(i, g[q].z, g[q].cre, g[q].cim, g[q].nt, g[q].has_im != 0, cr, ci);
+                if (g[q].tab) ztab_add(tab, g[q].tab, i, g[q].has_im != 0, cr, ci);
             }
             s += pr * cr - pi * ci;
         }
@@ -219,7 +303,7 @@ __device__ __forceinline__ R pauli_amp_sum(const R *__restrict__ amp, uint64_t i
 // sum in the state's precision).
 template <typename R, int NA, int QB, typename G>
 __device__ __forceinline__ void pauli_amp_sums(const R *__restrict__ amp, uint64_t i0, uint64_t stride, const G *g,
-                                               int ng, R (&s)[NA])
+                                               int ng, const R *tab, R (&s)[NA])
 {
     using V = typename Cplx<R>::V;
     V a[NA];
@@ -278,6 +362,10 @@ __device__ __forceinline__ void pauli_amp_sums(const R *__restrict__ amp, uint64
                         cr[k] += sg * fr;
                         if (him) ci[k] += sg * fi;
                     }
+                }
+                if (g[q].tab) {
+#pragma unroll
+                    for (int k = 0; k < NA; ++k) ztab_add(tab, g[q].tab, i0 + k * stride, him, cr[k], ci[k]);
                 }
             }
 #pragma unroll

@@ -233,7 +233,7 @@ struct PauliGroupAll {
     int nt;
     int zero_z;   // every z mask is 0: c(i) is the constant (c0re, c0im)
     int has_im;   // some coefficient has an imaginary part
-    int pad;
+    int tab;      // chunks of Z-term tables (pure-Z group), 0: none
     double c0re, c0im;
     float f0re, f0im;
     uint64_t z[kMaxTermsPerGroup];
@@ -244,14 +244,17 @@ constexpr size_t kPauliAllSmem = 200 * 1024;
 
 template <typename R>
 __global__ void __launch_bounds__(kThreads) pauli_all_kernel(const R *__restrict__ amp, uint64_t N,
-                                                             const PauliGroupAll *groups, int ng, double *part)
+                                                             const PauliGroupAll *groups, int ng, const R *ztab,
+                                                             int tab_words, double *part)
 {
     __shared__ double smem[kThreads / 32][1];
     extern __shared__ unsigned char sraw[];
     PauliGroupAll *g = reinterpret_cast<PauliGroupAll *>(sraw);
+    R *tab = reinterpret_cast<R *>(sraw + size_t(ng) * sizeof(PauliGroupAll));
     static_assert(sizeof(PauliGroupAll) % 8 == 0, "copied as 8-byte words");
     for (int k = threadIdx.x; k < ng * int(sizeof(PauliGroupAll) / 8); k += kThreads)
         reinterpret_cast<uint64_t *>(g)[k] = reinterpret_cast<const uint64_t *>(groups)[k];
+    for (int k = threadIdx.x; k < tab_words; k += kThreads) tab[k] = ztab[k];
     __syncthreads();
     CompSum<R> acc;
     // the terms of one amplitude are summed plainly (a few dozen of similar size);
@@ -262,11 +265,11 @@ __global__ void __launch_bounds__(kThreads) pauli_all_kernel(const R *__restrict
     uint64_t i = uint64_t(blockIdx.x) * kThreads + threadIdx.x;
     for (; i + 3 * S < N; i += 4 * S) {
         R s4[4];
-        pauli_amp_sums<R, 4, 4>(amp, i, S, g, ng, s4);
+        pauli_amp_sums<R, 4, 4>(amp, i, S, g, ng, tab, s4);
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc.add(s4[k]);
     }
-    for (; i < N; i += S) acc.add(pauli_amp_sum<R>(amp, i, g, ng));
+    for (; i < N; i += S) acc.add(pauli_amp_sum<R>(amp, i, g, ng, tab));
     double x[1] = {acc.value()};
     block_sum<1>(x, smem);
     if (threadIdx.x == 0) part[blockIdx.x] = x[0];
@@ -338,7 +341,7 @@ template <typename R> qv_status pauli_impl(qv_state *s, const qv_pauli_term *ter
         *out_host = 0;
         return QV_OK;
     }
-    if (ng * sizeof(PauliGroupAll) <= kPauliAllSmem) {
+    if (ng * sizeof(PauliGroupAll) + kZTabWords * sizeof(R) <= kPauliAllSmem) {
         // one pass over the state for all groups
         std::vector<PauliGroupAll> ga(ng);
         for (size_t q = 0; q < ng; ++q) {
@@ -361,16 +364,25 @@ template <typename R> qv_status pauli_impl(qv_state *s, const qv_pauli_term *ter
             a.f0re = float(a.c0re);
             a.f0im = float(a.c0im);
         }
-        const size_t gb = ng * sizeof(PauliGroupAll);
-        QV_TRY(ensure_scratch(s, gb + sizeof(double) * (grid + 1)));
+        // the pure-Z group's terms that lie inside one 8-bit chunk of the index go into tables
+        std::vector<R> htab = ztab_for_group<R>(s->n, ga);
+        for (PauliGroupAll &a : ga)
+            for (int k = 0; k < a.nt; ++k) {
+                a.fre[k] = float(a.cre[k]);
+                a.fim[k] = float(a.cim[k]);
+            }
+        const size_t gb = ng * sizeof(PauliGroupAll), tb = htab.size() * sizeof(R);
+        QV_TRY(ensure_scratch(s, gb + tb + sizeof(double) * (grid + 1)));
         char *base = static_cast<char *>(s->scratch.ptr);
         PauliGroupAll *dg = reinterpret_cast<PauliGroupAll *>(base);
-        double *part = reinterpret_cast<double *>(base + gb), *res = part + grid;
+        R *dtab = reinterpret_cast<R *>(base + gb);
+        double *part = reinterpret_cast<double *>(base + gb + tb), *res = part + grid;
         QV_TRY(copy_h2d(s, dg, ga.data(), gb));
+        if (tb) QV_TRY(copy_h2d(s, dtab, htab.data(), tb));
         QV_TRY(allow_smem(reinterpret_cast<const void *>(pauli_all_kernel<R>), int(kPauliAllSmem)));
         prof_bytes(s, QV_K_PAULI, double(dim(s)) * 2 * sizeof(R) * double(ng + 1));
-        QV_LAUNCH(s, QV_K_PAULI, pauli_all_kernel<R><<<grid, kThreads, gb, s->stream>>>(
-                                      static_cast<const R *>(s->amp), dim(s), dg, int(ng), part));
+        QV_LAUNCH(s, QV_K_PAULI, pauli_all_kernel<R><<<grid, kThreads, gb + tb, s->stream>>>(
+                                      static_cast<const R *>(s->amp), dim(s), dg, int(ng), dtab, int(htab.size()), part));
         QV_LAUNCH(s, QV_K_PAULI, sum_parts_kernel<<<1, 32, 0, s->stream>>>(part, int(grid), res));
         QV_TRY(ensure_host_out(s, 1));
         QV_TRY(copy_d2h(s, s->host_out, res, sizeof(double)));

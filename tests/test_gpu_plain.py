@@ -275,3 +275,46 @@ def test_sample_basis_and_ghz(qvlib, cuda):
     s = qv.qv_sample(h, np.linspace(0, 0.999, 200))
     assert set(int(x) for x in s) == {0, (1 << 20) - 1}
     qv.qv_destroy(h)
+
+
+def _z_heavy_terms(n, seed):
+    """Z strings of every shape the pure-Z tables handle: inside one 8-bit chunk
+    of the index, spanning two chunks, on the top qubits, the identity, plus a
+    few X and Y terms."""
+    rng = W.SplitMix64(seed)
+    terms = [(0.75, 0, 0)]                                        # identity
+    for i in range(n - 1):
+        terms.append((1.0 - 0.01 * i, 0, (1 << i) | (1 << (i + 1))))  # ZZ chain: within and across chunks
+    for i in range(0, n, 3):
+        terms.append((0.3, 0, 1 << i))                            # single Z
+    u = rng.integers(1, (1 << n) - 1, 6)
+    for k in range(6):
+        terms.append((0.2 * (k + 1), 0, int(u[k])))               # wide Z strings (residual terms)
+    terms += [(0.5, 1 << (n - 1), 0), (0.25, 0b101, 0b100), (-0.4, 1 << 3, 1 << 7)]
+    return terms
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("n", [12, 20, 27])
+def test_pauli_z_tables(qvlib, orc, cuda, dtype, n):
+    """<psi|H|psi> and H|psi> with a pure-Z group large enough for the chunk
+    tables (terms inside 8-bit chunks tabled, the rest summed term by term),
+    against the oracle on a random state."""
+    qv = qvlib
+    terms = _z_heavy_terms(n, 900 + n)
+    psi = W.random_state(n, 31 + n)
+    h = qv.qv_create(n, dtype)
+    out = qv.qv_create(n, dtype)
+    try:
+        qv.qv_set_state(h, psi)
+        got = qv.qv_expect_pauli(h, terms)
+        ref = psi.astype(np.complex64).astype(np.complex128) if dtype == 0 else psi
+        scale = sum(abs(t[0]) for t in terms)
+        assert abs(got - orc.expect_terms(ref, terms)) <= (2e-5 if dtype == 0 else 1e-11) * scale
+        qv.qv_apply_pauli(h, terms, out)
+        want = orc.apply_pauli_sum(ref.copy(), terms)
+        err = np.linalg.norm(qv.qv_get_state(out).astype(np.complex128) - want) / np.linalg.norm(want)
+        assert err <= (5e-6 if dtype == 0 else 1e-13)
+    finally:
+        qv.qv_destroy(h)
+        qv.qv_destroy(out)
