@@ -181,3 +181,26 @@ def test_ptxas_report_reads_every_function(tmp_path):
     exe = tmp_path / "t"
     subprocess.check_call(["g++", "-std=c++17", "-O1", "-o", str(exe), str(src)])
     assert subprocess.check_output([str(exe)]).decode().split() == ["128", "1", "96", "0", "-1"]
+
+
+def test_pure_z_tables_host(tmp_path):
+    """The Pauli kernels' tables of a pure-Z group (host construction): tables
+    plus the terms left out equal the term-by-term coefficient at random
+    indices, for 5 to 40 qubits; every term inside one 8-bit chunk is tabled."""
+    import shutil
+    import subprocess
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not found")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    exe = tmp_path / "ztab"
+    subprocess.check_call([nvcc, "-std=c++17", "-O1", "-gencode", "arch=compute_103a,code=sm_103a",
+                           "-I", os.path.join(root, "paper_2508_15545_gb300", "csrc"),
+                           "-o", str(exe), os.path.join(root, "tests", "ztab_check.cu")])
+    out = subprocess.check_output([str(exe)]).decode().split("\n")
+    assert out[-2] == "bad 0", out
+    rows = {int(l.split()[1]): l.split() for l in out if l.startswith("n ")}
+    # n = 20: chunks of bits 0-7, 8-15, 16-19; the chain's 17 terms inside a chunk
+    # and the identity are tabled; (7, 8) and (15, 16) are not
+    assert rows[20][3] == "3" and int(rows[20][5]) >= 18
+    assert rows[40][3] == "5"
