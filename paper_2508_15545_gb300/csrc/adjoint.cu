@@ -348,7 +348,10 @@ qv_status pauli_apply_impl(qv_state *s, const void *src, void *dst, const qv_pau
         gg.c0im = R(c0i);
     }
     // the pure-Z group's terms that lie inside one 8-bit chunk of the index go into tables
-    const std::vector<R> htab = ztab_for_group<R>(s->n, groups);
+    // (only when the tables fit in shared memory beside the groups)
+    const std::vector<R> htab = groups.size() * sizeof(PauliGroupA<R>) + kZTabWords * sizeof(R) <= 200 * 1024
+                                    ? ztab_for_group<R>(s->n, groups)
+                                    : std::vector<R>();
     const size_t gbytes = groups.size() * sizeof(PauliGroupA<R>), tbytes = htab.size() * sizeof(R);
     if (gbytes + tbytes > 200 * 1024)
         return fail(QV_ERR_UNSUPPORTED, "Hamiltonian too large (%zu X-mask groups)", groups.size());

@@ -589,7 +589,10 @@ qv_status build(qv_batch *b, const qv_batch_item *items, size_t count, const qv_
         // the pure-Z group's terms that lie inside one 8-bit chunk of the index go into tables
         int maxn = 0;
         for (int v : nq) maxn = std::max(maxn, v);
-        const std::vector<R> htab = ztab_for_group<R>(maxn, hg);
+        // (only when the tables fit in shared memory beside the groups)
+        const std::vector<R> htab = hg.size() * sizeof(BGroup) + kZTabWords * sizeof(R) <= 200 * 1024
+                                        ? ztab_for_group<R>(maxn, hg)
+                                        : std::vector<R>();
         for (BGroup &gg : hg)
             for (int k = 0; k < gg.nt; ++k) {
                 gg.fre[k] = float(gg.cre[k]);

@@ -211,3 +211,30 @@ def test_adjoint_cache_follows_the_angles(qvlib, orc, cuda):
                 assert np.max(np.abs(g - ref)) <= 1e-4, rep
     finally:
         qv.qv_destroy(h)
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_apply_pauli_many_groups(qvlib, orc, cuda, dtype):
+    """H|psi> with so many X-mask groups (a pure-Z chain and 189 single-term X
+    strings for complex64, 119 for complex128) that the groups fill the
+    kernel's shared memory: the pure-Z group is then summed term by term
+    instead of through chunk tables, and the result equals the oracle's."""
+    qv = qvlib
+    n = 12
+    rng = W.SplitMix64(4343)
+    masks = sorted(set(int(m) for m in rng.integers(1, (1 << n) - 1, 400)))[:189 if dtype == 0 else 119]
+    terms = [(1.0, 0, (1 << i) | (1 << (i + 1))) for i in range(n - 1)] + \
+            [(0.01 * (k + 1), m, 0) for k, m in enumerate(masks)]
+    psi = W.random_state(n, 4344)
+    a = qv.qv_create(n, dtype)
+    b = qv.qv_create(n, dtype)
+    try:
+        qv.qv_set_state(a, psi)
+        qv.qv_apply_pauli(a, terms, b)
+        ref = psi.astype(np.complex64).astype(np.complex128) if dtype == 0 else psi
+        want = orc.apply_pauli_sum(ref, terms)
+        tol = 2e-5 if dtype == 0 else 1e-12
+        assert np.max(np.abs(qv.qv_get_state(b) - want)) <= tol * sum(abs(t[0]) for t in terms)
+    finally:
+        qv.qv_destroy(a)
+        qv.qv_destroy(b)

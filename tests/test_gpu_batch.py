@@ -242,3 +242,27 @@ def test_batch_members_on_side_streams(qvlib, orc, cuda):
     finally:
         for h in states:
             qv.qv_destroy(h)
+
+
+def test_batch_energy_many_groups(qvlib, orc, cuda):
+    """A Hamiltonian of 95 X-mask groups (a pure-Z chain and 94 single-term X
+    strings): the groups fill the batched kernel's shared memory, so the pure-Z
+    group is summed term by term instead of through chunk tables; energies
+    equal the oracle's."""
+    qv = qvlib
+    n = 12
+    rng = W.SplitMix64(4242)
+    masks = sorted(set(int(m) for m in rng.integers(1, (1 << n) - 1, 200)))[:94]
+    terms = [(1.0, 0, (1 << i) | (1 << (i + 1))) for i in range(n - 1)] + \
+            [(0.01 * (k + 1), m, 0) for k, m in enumerate(masks)]
+    circuits = [W.random_circuit(n, 4, seed=4300 + c) for c in range(3)]
+    states = [qv.qv_create(n, 0) for _ in circuits]
+    try:
+        b = qv.Batch(list(zip(states, circuits)), terms)
+        e = b.run()
+        for c, g in enumerate(circuits):
+            assert e[c] == pytest.approx(orc.energy(n, g, terms), abs=2e-5 * sum(abs(t[0]) for t in terms)), c
+        b.close()
+    finally:
+        for h in states:
+            qv.qv_destroy(h)
